@@ -1,0 +1,205 @@
+"""Pins of the CPU oracle against facts fixed outside it (no GPU).
+
+Each test checks the oracle against something other than itself: a published
+closed form, a symmetry of the S-matrix, an independent brute-force
+computation, or a count printed in the paper (tests/golden).
+"""
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import closed_form, color, topology
+from paper_2510_05392_gb300 import phasespace as ps
+
+GS = math.sqrt(4 * math.pi * 0.118)
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_table_complexity.json")
+
+
+def _events(ng, nevt, seed, sqrts=1500.0):
+    kw = dict(ptmin=20.0, drmin=0.4) if ng else {}
+    return ps.generate(nevt, ng, sqrts, seed, **kw)
+
+
+# ---------------------------------------------------------------- colour ----
+
+def test_color_matrix_two_gluons_closed_form():
+    # C_F^2 N = 16/3 on the diagonal, (C_F - C_A/2) C_F N = -2/3 off it
+    Chat, D, perms = color.color_matrix(2)
+    assert D == 3
+    assert Chat == [[16, -2], [-2, 16]]
+    assert perms == [(0, 1), (1, 0)]
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5])
+def test_color_matrix_trace_pin(n):
+    # Tr C = n! C_F^n N: every diagonal entry is Tr(t^a1..t^an t^an..t^a1)
+    from fractions import Fraction
+    Chat, D, _ = color.color_matrix(n)
+    assert Fraction(sum(Chat[i][i] for i in range(len(Chat))), D) == \
+        math.factorial(n) * 3 * Fraction(4, 3) ** n
+
+
+def _gell_mann():
+    l = np.zeros((8, 3, 3), dtype=complex)
+    l[0][0, 1] = l[0][1, 0] = 1
+    l[1][0, 1], l[1][1, 0] = -1j, 1j
+    l[2][0, 0], l[2][1, 1] = 1, -1
+    l[3][0, 2] = l[3][2, 0] = 1
+    l[4][0, 2], l[4][2, 0] = -1j, 1j
+    l[5][1, 2] = l[5][2, 1] = 1
+    l[6][1, 2], l[6][2, 1] = -1j, 1j
+    l[7][0, 0] = l[7][1, 1] = 1 / math.sqrt(3)
+    l[7][2, 2] = -2 / math.sqrt(3)
+    return l / 2
+
+
+@pytest.mark.parametrize("n", [2, 3, 4])
+def test_color_matrix_brute_force_traces(n):
+    """Sum explicit Gell-Mann generators over every colour index."""
+    t = _gell_mann()
+    perms = color.gluon_orderings(n)
+    rows = []
+    for s in perms:
+        # T_s[a_1..a_n] = t^{a_s1} ... t^{a_sn} for every assignment of a's
+        acc = None
+        for pos in range(n):
+            g = s[pos]
+            shape = [1] * n + [3, 3]
+            shape[g] = 8
+            tg = t.reshape(shape)
+            acc = tg if acc is None else np.einsum("...ij,...jk->...ik", acc, tg)
+        acc = np.broadcast_to(acc, [8] * n + [3, 3])
+        rows.append(acc.reshape(-1))
+    T = np.array(rows)
+    C_bf = (T.conj() @ T.T)
+    assert np.abs(C_bf.imag).max() < 1e-12
+    Chat, D, p2 = color.color_matrix(n)
+    assert list(p2) == list(perms)
+    np.testing.assert_allclose(C_bf.real, np.array(Chat) / D, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5])
+def test_color_matrix_symmetric_psd(n):
+    Chat, D, _ = color.color_matrix(n)
+    C = np.array(Chat, dtype=float)
+    assert np.array_equal(C, C.T)
+    assert np.linalg.eigvalsh(C).min() > -1e-9 * np.abs(C).max()
+
+
+# ------------------------------------------------------------ diagrams -----
+
+def test_counts_against_paper_table():
+    g = json.load(open(GOLDEN))["processes"]
+    for proc, row in g.items():
+        n = oracle.ngluons(proc)
+        assert len(color.gluon_orderings(n)) == row["colors"]
+        assert 2 ** (n + 2) == row["helicities"]
+        if n <= 6:
+            assert topology.count_diagrams(n) == row["diagrams"], proc
+
+
+# ------------------------------------------------------- matrix elements ---
+
+def test_closed_form_ggtt_zero_width():
+    p = _events(0, 256, 101, sqrts=1000.0)
+    a = oracle.me(p, wt=0.0)
+    b = closed_form.ggqq_averaged(p, 173.0, GS)
+    # both sides round differently; near-collinear tops amplify it to ~1e-13
+    assert np.abs(a / b - 1).max() < 1e-12
+    assert np.median(np.abs(a / b - 1)) < 1e-14
+
+
+def test_closed_form_massless_limit():
+    # m -> 0 reduces Combridge to the textbook g g -> q qbar result
+    p = ps.generate(64, 0, 1000.0, 5, mt=0.0)
+    # put the final state exactly on the light cone (RAMBO leaves p^2 ~ 1e-10)
+    p[:, 2:, 0] = np.sqrt((p[:, 2:, 1:] ** 2).sum(-1))
+    a = oracle.me(p, mt=0.0, wt=0.0)
+    s = 2 * (p[:, 0, 0] * p[:, 1, 0] - (p[:, 0, 1:] * p[:, 1, 1:]).sum(1))
+    t = -2 * (p[:, 0, 0] * p[:, 2, 0] - (p[:, 0, 1:] * p[:, 2, 1:]).sum(1))
+    u = -2 * (p[:, 1, 0] * p[:, 2, 0] - (p[:, 1, 1:] * p[:, 2, 1:]).sum(1))
+    textbook = GS ** 4 * ((t * t + u * u) / (6 * t * u) - 3 * (t * t + u * u) / (8 * s * s))
+    # t = -2 p1.p3 loses digits as s/|t| grows (near-collinear events): scale the bound
+    cond = s / np.minimum(np.abs(t), np.abs(u))
+    assert np.all(np.abs(a / textbook - 1) < 1e-13 * cond)
+    assert np.median(np.abs(a / textbook - 1)) < 1e-14
+
+
+@pytest.mark.parametrize("ng", [0, 1, 2, 3])
+def test_gauge_invariance_every_ordering(ng):
+    """eps_i -> k_i makes every colour-ordered amplitude vanish (zero width)."""
+    n = ng + 2
+    p = _events(ng, 2, 200 + ng)
+    nhel = 1 << (n + 2)
+    for e in range(len(p)):
+        # scale: the largest amplitude of this event over all helicities
+        ref = max(np.abs(oracle.amplitudes(p[e], h, wt=0.0)).max() for h in range(nhel))
+        for h in sorted({0, 1, nhel // 3, nhel - 1}):
+            for leg in range(n):
+                ip = leg if leg < 2 else leg + 2
+                g = oracle.amplitudes(p[e], h, gauge_leg=leg, wt=0.0)
+                assert np.abs(g).max() / p[e, ip, 0] <= 1e-10 * ref
+
+
+def _boost(beta):
+    beta = np.asarray(beta, float)
+    b2 = beta @ beta
+    g = 1 / math.sqrt(1 - b2)
+    L = np.eye(4)
+    L[0, 0] = g
+    L[0, 1:] = L[1:, 0] = g * beta
+    L[1:, 1:] += (g - 1) * np.outer(beta, beta) / b2
+    return L
+
+
+@pytest.mark.parametrize("ng", [0, 1, 2, 3])
+def test_lorentz_invariance_zero_width(ng):
+    p = _events(ng, 4 if ng < 3 else 2, 300 + ng)
+    rng = np.random.default_rng(ng)
+    m = oracle.me(p, wt=0.0)
+    for _ in range(2):
+        beta = rng.uniform(-0.5, 0.5, 3)
+        L = _boost(beta)
+        # also rotate: random orthogonal 3x3
+        q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+        R = np.eye(4)
+        R[1:, 1:] = q * np.sign(np.linalg.det(q))
+        pb = p @ (L @ R).T
+        mb = oracle.me(pb, wt=0.0)
+        assert np.abs(mb / m - 1).max() < 1e-11
+
+
+@pytest.mark.parametrize("ng", [1, 2, 3])
+def test_bose_symmetry_with_width(ng):
+    p = _events(ng, 4 if ng < 3 else 2, 400 + ng)
+    m = oracle.me(p)
+    sw = p[:, [1, 0, 2, 3] + list(range(4, 4 + ng))]
+    assert np.abs(oracle.me(sw) / m - 1).max() < 1e-12
+    for perm in list(itertools.permutations(range(4, 4 + ng)))[1:3]:
+        q = p[:, [0, 1, 2, 3] + list(perm)]
+        assert np.abs(oracle.me(q) / m - 1).max() < 1e-12
+
+
+def test_helicity_sum_equals_total():
+    p = _events(1, 3, 500)
+    m, mh = oracle.me(p, per_helicity=True)
+    np.testing.assert_allclose(mh.sum(1), m, rtol=1e-14)
+
+
+@pytest.mark.parametrize("ng", [0, 1, 2])
+def test_helicity_mask_all_good(ng):
+    # table "complexity": all helicities contribute for these processes
+    p = _events(ng, 16, 600 + ng)
+    mask = oracle.good_helicity_mask(p)
+    assert mask.all()
+
+
+def test_width_is_a_small_effect():
+    p = _events(2, 4, 700)
+    r = oracle.me(p) / oracle.me(p, wt=0.0)
+    assert np.all(np.abs(r - 1) < 1e-2)

@@ -1,0 +1,138 @@
+/*
+ * mgpu -- leading-order QCD matrix elements for g g -> t t~ + n g on one
+ * NVIDIA GB300 (sm_103a).  C ABI.
+ *
+ * What the library computes is the per-event matrix element engine of the
+ * paper (Sec. 3, "sigmaKin": input 4*npar doubles per event, output one
+ * matrix element per event): external wavefunctions, internal wavefunctions
+ * and amplitudes of every Feynman diagram, accumulated into colour-flow
+ * amplitudes ("jamps"), contracted with the colour matrix (Sec. 5, Eq. "jcj":
+ * J^H C J = A^T C A + B^T C B with J = A + iB), summed over the good
+ * helicities (Sec. 3 and Sec. 8, helicity filtering) and averaged over
+ * initial spins/colours and identical final gluons.
+ *
+ * Conventions
+ *   particle order   g1 g2 t t~ g5 ... g_npar (g1 along +z, g2 along -z)
+ *   momenta          (E, px, py, pz) in GeV, float64, layout [nevt][npar][4]
+ *                    contiguous, 8-byte aligned, in device memory on the
+ *                    process's device
+ *   output           float64 [nevt] in device memory, GeV^(4-2*npar)
+ *   helicity index   h in [0, 2^npar): bit (npar-1-i) set <=> particle i has
+ *                    positive helicity
+ *   streams          every compute call is asynchronous and ordered on the
+ *                    given cudaStream_t (NULL = legacy default stream); the
+ *                    library never synchronises the device inside
+ *                    mg_sigmakin
+ *
+ * Ownership: the caller owns all momentum/output buffers.  The library owns
+ * the opaque process handle, its device tables and its workspaces, all
+ * released by mg_process_destroy.
+ *
+ * Errors: every function returns MG_OK (0) or a negative status; nothing
+ * aborts, exits or traps.  mg_status_string() names a status.
+ */
+#ifndef MGPU_H
+#define MGPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    MG_OK = 0,
+    MG_ERR_BAD_PROCESS = -1,   /* unknown or unsupported process string      */
+    MG_ERR_BAD_ARG = -2,       /* null/misaligned/host pointer, bad size/flag */
+    MG_ERR_NOT_FILTERED = -3,  /* mg_sigmakin before mg_filter_helicities     */
+    MG_ERR_CUDA = -4,          /* a CUDA runtime call failed                  */
+    MG_ERR_DEVICE_TIMEOUT = -5,/* a bounded device-side wait gave up          */
+    MG_ERR_NO_MEMORY = -6,     /* device allocation failed                    */
+    MG_ERR_UNSUPPORTED = -7    /* feature not available for this process     */
+};
+
+enum { MG_HEL_FILTERED = 0, MG_HEL_ALL = 1 };
+enum { MG_FP64 = 0, MG_MIXED_BF16 = 1 };
+
+typedef struct mg_process mg_process; /* opaque, library-owned */
+
+typedef struct {
+    double mt;       /* top mass [GeV]                                      */
+    double wt;       /* top width [GeV], used in every top propagator        */
+    double alphas;   /* fixed strong coupling, g_s = sqrt(4 pi alphas)      */
+    int hel_mode;    /* MG_HEL_FILTERED (filter first) or MG_HEL_ALL        */
+    int precision;   /* MG_FP64 (all FP64) or MG_MIXED_BF16 (FP64 diagrams, */
+                     /* tensor-core colour sum)                             */
+} mg_params;
+
+typedef struct {
+    int npar;             /* external particles                          */
+    int ngluon;           /* gluons, incoming included                   */
+    int ndiagrams;        /* Feynman diagrams (4-gluon vertex counted once) */
+    int nterms;           /* diagram terms (each 4-gluon vertex has 3)   */
+    int ncolor;           /* colour flows                                 */
+    int nhel;             /* 2^npar helicity combinations                 */
+    int ngood;            /* good helicities (-1 before filtering)        */
+    int nslot;            /* wavefunction slots per thread                */
+    int nops;             /* wavefunction/amplitude operations            */
+    int njamp_updates;    /* jamp updates per helicity                    */
+    int64_t denom;        /* colour-matrix common denominator D           */
+    double iden;          /* averaging factor                             */
+    double flops_diagram; /* algorithmic FP64 flops per helicity: diagrams */
+    double flops_colour;  /* algorithmic FP64 flops per helicity: colour sum */
+} mg_info;
+
+/* Create a process from its description, e.g. "g g > t t~ g g".  Supported:
+ * g g > t t~ followed by 0..4 final gluons.  Uploads the process tables to
+ * the current CUDA device.  params may be NULL (mt 173, wt 1.4915,
+ * alphas 0.118, filtered helicities, FP64). */
+int mg_process_create(const char *process, const mg_params *params, mg_process **out);
+
+/* Helicity filter (Sec. 3 and Sec. 8 of the paper: keep the helicities with
+ * a non-zero contribution).  Evaluates all 2^npar helicities in parallel on
+ * the n test events momenta_dev[n][npar][4] and keeps h when
+ * |M_h|^2 > 1e-14 * max_h' |M_h'|^2 on any of them.  Synchronises the stream
+ * (initialisation step).  n in [1, 65536].  *ngood_out may be NULL. */
+int mg_filter_helicities(mg_process *p, const double *momenta_dev, int64_t n, void *stream,
+                         int *ngood_out);
+
+/* Matrix elements of nevt events: me_out_dev[nevt] (float64, device).
+ * nevt = 0 is a no-op.  Asynchronous on stream.  Requires a prior
+ * mg_filter_helicities unless hel_mode == MG_HEL_ALL.  Non-finite momenta
+ * give non-finite results (not checked). */
+int mg_sigmakin(mg_process *p, const double *momenta_dev, int64_t nevt, double *me_out_dev,
+                void *stream);
+
+/* Per-helicity contributions: me_hel_dev[nevt][2^npar] (float64, device),
+ * already averaged (their sum over h is the matrix element); helicities that
+ * are not good are written as 0.  me_out_dev may be NULL. */
+int mg_sigmakin_hel(mg_process *p, const double *momenta_dev, int64_t nevt, double *me_out_dev,
+                    double *me_hel_dev, void *stream);
+
+/* Launch shape: threads per event (1..32, power of two) and threads per
+ * block (multiple of 32, <= 1024).  0 keeps the current value. */
+int mg_set_launch(mg_process *p, int threads_per_event, int block);
+
+int mg_process_info(const mg_process *p, mg_info *out);
+
+/* Integer colour matrix D*C (row-major ncolor x ncolor) and D, exactly as
+ * the colour sum uses them.  Flow s is the string t^{a_s1}..t^{a_sn} with
+ * orderings in lexicographic permutation order of the gluons (g1 g2 g5 ...). */
+int mg_color_matrix(const mg_process *p, int64_t *ints_out, int64_t *denom_out);
+
+/* Good-helicity mask [2^npar] (1 = good) after filtering (or all ones in
+ * MG_HEL_ALL mode).  MG_ERR_NOT_FILTERED before. */
+int mg_helicity_mask(const mg_process *p, uint8_t *mask_out);
+
+void mg_process_destroy(mg_process *p);
+
+const char *mg_status_string(int status);
+
+/* Last CUDA error string seen by the library on this thread ("" if none). */
+const char *mg_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

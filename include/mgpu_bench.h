@@ -1,0 +1,23 @@
+/*
+ * Measurement helpers of the mgpu library (not part of the matrix-element
+ * method).
+ */
+#ifndef MGPU_BENCH_H
+#define MGPU_BENCH_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* FP64 fused multiply-add throughput of the current device.  Launches
+ * `blocks` x 256 threads that each run `iters` rounds of 16 independent FMA
+ * chains (no memory traffic), times `reps` launches with CUDA events on a
+ * private stream after one warm-up, and writes the best rate in FP64 flops/s
+ * (FMA = 2 flops) to *flops_out.  blocks <= 0 picks 8 per SM.  Returns 0 or
+ * a negative mgpu status (MG_ERR_CUDA on a CUDA failure). */
+int mg_probe_fp64_peak(int blocks, int iters, int reps, double *flops_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,119 @@
+"""Emit the process tables compiled into the CUDA library.
+
+For every supported process the generated include file holds:
+  OPS    int32[nops][8]   the wavefunction/amplitude program (program.py)
+  SCAT   int32[nscat]     jamp scatter entries (flow * 4 + coefficient code)
+  CHAT   int32[nc][nc]    integer colour matrix D * C (colour.py)
+and one registry row with the sizes, the common denominator D, the averaging
+factor and the algorithmic FP64 operation counts per helicity.
+
+Usage: python -m paper_2510_05392_gb300.compiler.emit OUT.inc [maxgluons]
+"""
+from __future__ import annotations
+
+import math
+import sys
+
+from . import colour, program
+
+PROCESSES = [
+    ("ggtt", "g g > t t~"),
+    ("ggttg", "g g > t t~ g"),
+    ("ggttgg", "g g > t t~ g g"),
+    ("ggttggg", "g g > t t~ g g g"),
+    ("ggttgggg", "g g > t t~ g g g g"),
+]
+
+# Algorithmic FP64 operations (an FMA counts 2 flops, mul/add 1) of each op
+# for one helicity, from the arithmetic the operation must do, not from the
+# instructions the compiler emits.  Complex a*b = 6 flops, a*b+c = 8.
+FLOPS = {
+    program.OP_EXT_G: 0,     # external states: counted separately (per event)
+    program.OP_EXT_UB: 0,
+    program.OP_EXT_V: 0,
+    # V3: 3 complex Minkowski dots (one complex x complex: 4*8-2 = 30, two
+    # real x complex: 2*(4*4-2) = 28), 3 complex scalings by 1/P^2 (6),
+    # 4 components of j*d + s2*J2 - s1*J1 (4*(2 + 8 + 8) = 72)
+    program.OP_V3: 30 + 28 + 6 + 72,
+    # V4: 3 complex dots (90), 3 structures x 4 components of a*X - b*Y
+    # (3*4*14 = 168), 3 x 4 complex scalings by 1/P^2 (24... as 3 scalars x2)
+    program.OP_V4: 90 + 168 + 18,
+    # FPRE/FSUF: Jslash blocks (8 complex adds = 16), two 2x2 complex
+    # mat-vecs (2*(4*6+2*2) = 56), (q+m) blocks: two 2x2 mat-vecs with
+    # real-or-imaginary entries (2*(4*4+2*2) = 40) plus mass terms (8*2 = 16),
+    # complex scale by 1/den (4*6 = 24)
+    program.OP_FPRE: 16 + 56 + 40 + 16 + 24,
+    program.OP_FSUF: 16 + 56 + 40 + 16 + 24,
+    program.OP_XROW: 16 + 56,
+    program.OP_YCOL: 16 + 56,
+    # bilinear: 8 complex products (48) + 12 complex adds (24)
+    program.OP_BIL: 48 + 24,
+    # amplitudes: 4 complex products + 3 complex adds
+    program.OP_AMP_SS: 4 * 6 + 3 * 2,
+    program.OP_AMP_VV: 4 * 6 + 3 * 2,
+}
+JAMP_UPDATE_FLOPS = 2
+
+
+def algorithmic_flops(prog: program.Program) -> dict:
+    """FP64 flops per helicity: diagrams (ops + jamp updates) and colour sum
+    (symmetric quadratic form over A and B: 2 * nc^2 multiply-adds)."""
+    diag = sum(FLOPS[op[0]] for op in prog.ops) + JAMP_UPDATE_FLOPS * len(prog.scatter)
+    nc = prog.ncolor
+    csum = 2 * (nc * (nc + 1) // 2) * 2 + 2 * nc
+    return dict(diagram=diag, colour=csum)
+
+
+def _arr(name, vals, per_line=16):
+    out = [f"static const int32_t {name}[{max(1, len(vals))}] = {{"]
+    for i in range(0, len(vals), per_line):
+        out.append("  " + ",".join(str(int(v)) for v in vals[i:i + per_line]) + ",")
+    if not vals:
+        out.append("  0")
+    out.append("};")
+    return "\n".join(out)
+
+
+def emit(path: str, max_gluons: int = 6, list_path: str | None = None) -> None:
+    """Write the table include file ``path`` and, next to it (or at
+    ``list_path``), mg_proc_list.h with one X(index, ngluon, nslot, ncolor)
+    entry per process for the kernel instantiations."""
+    lines = ["/* generated by paper_2510_05392_gb300.compiler.emit -- do not edit */",
+             "#pragma once", "#include <stdint.h>", ""]
+    rows = []
+    xlist = []
+    for name, proc in PROCESSES:
+        n = 2 + len(proc.split()) - 5
+        if n > max_gluons:
+            continue
+        prog = program.build_program(n)
+        Chat, D, perms = colour.colour_matrix(n)
+        assert [tuple(p) for p in perms] == [tuple(p) for p in prog.perms]
+        flat_ops = [v for r in prog.ops for v in r]
+        flat_c = [v for r in Chat for v in r]
+        lines.append(_arr(f"OPS_{name}", flat_ops))
+        lines.append(_arr(f"SCAT_{name}", prog.scatter))
+        lines.append(_arr(f"CHAT_{name}", flat_c))
+        fl = algorithmic_flops(prog)
+        iden = 256 * math.factorial(n - 2)
+        rows.append(
+            f'  {{"{name}", "{proc}", {n}, {n + 2}, {prog.ndiagrams}, {prog.nterms}, '
+            f'{prog.ncolor}, {prog.nslot}, {len(prog.ops)}, {len(prog.scatter)}, {D}LL, '
+            f'{iden}.0, {fl["diagram"]}.0, {fl["colour"]}.0, OPS_{name}, SCAT_{name}, CHAT_{name}}},')
+        xlist.append(f"X({len(rows) - 1}, {n}, {prog.nslot}, {prog.ncolor})")
+        lines.append("")
+    lines.append("static const mg_proc_table MG_PROC_TABLES[] = {")
+    lines.extend(rows)
+    lines.append("};")
+    lines.append(f"static const int MG_NPROC_TABLES = {len(rows)};")
+    with open(path, "w") as f:
+        f.write("\n".join(lines) + "\n")
+    import os
+    lp = list_path or os.path.join(os.path.dirname(path), "mg_proc_list.h")
+    with open(lp, "w") as f:
+        f.write("/* generated by paper_2510_05392_gb300.compiler.emit -- do not edit */\n"
+                "#pragma once\n#define MG_PROC_LIST(X) " + " ".join(xlist) + "\n")
+
+
+if __name__ == "__main__":
+    emit(sys.argv[1], int(sys.argv[2]) if len(sys.argv) > 2 else 6)

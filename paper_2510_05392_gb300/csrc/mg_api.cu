@@ -1,0 +1,350 @@
+// Host runtime behind the C ABI declared in include/mgpu.h: process
+// registry, device tables, argument checks, helicity filtering and the
+// launch of the diagram kernel.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <string>
+
+#include "mg_internal.h"
+#include "mgpu.h"
+
+struct mg_process {
+    const mg_proc_table *tab;
+    int table_index;
+    mg_params par;
+    int device;
+    int32_t *d_ops;
+    int32_t *d_scat;
+    double *d_cup;
+    int *d_hel;          // good-helicity list (device)
+    int ngood;           // -1 until filtered
+    uint8_t mask[256];
+    int tpe, block;      // launch shape
+    double factor;
+};
+
+namespace {
+
+thread_local char g_cuda_err[256] = "";
+
+int cuda_fail(cudaError_t e) {
+    snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+    return MG_ERR_CUDA;
+}
+
+#define MG_CUDA(call)                          \
+    do {                                       \
+        cudaError_t _e = (call);               \
+        if (_e != cudaSuccess) return cuda_fail(_e); \
+    } while (0)
+
+std::string normalise(const char *s) {
+    std::string out;
+    bool sp = true;
+    for (const char *c = s; *c; c++) {
+        if (*c == ' ' || *c == '\t' || *c == '\n') {
+            if (!sp) out.push_back(' ');
+            sp = true;
+        } else {
+            out.push_back(*c);
+            sp = false;
+        }
+    }
+    while (!out.empty() && out.back() == ' ') out.pop_back();
+    return out;
+}
+
+// A device pointer usable by this process: non-null, 8-byte aligned, device
+// (or managed) memory of the process's device.
+int check_dev_ptr(const void *ptr, int device) {
+    if (!ptr) return MG_ERR_BAD_ARG;
+    if (reinterpret_cast<uintptr_t>(ptr) % 8) return MG_ERR_BAD_ARG;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, ptr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return MG_ERR_BAD_ARG;
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return MG_ERR_BAD_ARG;
+    if (at.type == cudaMemoryTypeDevice && at.device != device) return MG_ERR_BAD_ARG;
+    return MG_OK;
+}
+
+mg_dev_proc dev_view(const mg_process *p) {
+    mg_dev_proc d;
+    d.table_index = p->table_index;
+    d.ops = p->d_ops;
+    d.nops = p->tab->nops;
+    d.scat = p->d_scat;
+    d.cup = p->d_cup;
+    d.ncolor = p->tab->ncolor;
+    d.mt = p->par.mt;
+    d.wt = p->par.wt;
+    d.factor = p->factor;
+    return d;
+}
+
+void free_proc(mg_process *p) {
+    if (!p) return;
+    cudaFree(p->d_ops);
+    cudaFree(p->d_scat);
+    cudaFree(p->d_cup);
+    cudaFree(p->d_hel);
+    free(p);
+}
+
+int set_hel_list(mg_process *p, const uint8_t *mask) {
+    const int nhel = 1 << p->tab->npar;
+    int list[256];
+    int ng = 0;
+    for (int h = 0; h < nhel; h++) {
+        p->mask[h] = mask[h] ? 1 : 0;
+        if (mask[h]) list[ng++] = h;
+    }
+    if (ng > 0) MG_CUDA(cudaMemcpy(p->d_hel, list, sizeof(int) * ng, cudaMemcpyHostToDevice));
+    p->ngood = ng;
+    return MG_OK;
+}
+
+int default_tpe(int npar) {
+    // threads per event: enough helicity slots per event for small
+    // processes, one thread per event for the large ones
+    switch (npar) {
+        case 4: return 16;
+        case 5: return 8;
+        case 6: return 4;
+        case 7: return 2;
+        default: return 1;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mg_status_string(int s) {
+    switch (s) {
+        case MG_OK: return "ok";
+        case MG_ERR_BAD_PROCESS: return "unknown or unsupported process";
+        case MG_ERR_BAD_ARG: return "bad argument";
+        case MG_ERR_NOT_FILTERED: return "helicities not filtered";
+        case MG_ERR_CUDA: return "CUDA error";
+        case MG_ERR_DEVICE_TIMEOUT: return "device wait timed out";
+        case MG_ERR_NO_MEMORY: return "out of device memory";
+        case MG_ERR_UNSUPPORTED: return "unsupported";
+        default: return "unknown status";
+    }
+}
+
+const char *mg_last_cuda_error(void) { return g_cuda_err; }
+
+int mg_process_create(const char *process, const mg_params *params, mg_process **out) {
+    if (!process || !out) return MG_ERR_BAD_ARG;
+    *out = nullptr;
+    mg_params par = {173.0, 1.4915, 0.118, MG_HEL_FILTERED, MG_FP64};
+    if (params) par = *params;
+    if (!(par.mt > 0.0) || !(par.wt >= 0.0) || !(par.alphas > 0.0)) return MG_ERR_BAD_ARG;
+    if (par.hel_mode != MG_HEL_FILTERED && par.hel_mode != MG_HEL_ALL) return MG_ERR_BAD_ARG;
+    if (par.precision != MG_FP64 && par.precision != MG_MIXED_BF16) return MG_ERR_BAD_ARG;
+    if (par.precision == MG_MIXED_BF16) return MG_ERR_UNSUPPORTED;
+    int ntab = 0;
+    const mg_proc_table *tabs = mg_tables(&ntab);
+    const std::string want = normalise(process);
+    int idx = -1;
+    for (int i = 0; i < ntab; i++)
+        if (want == tabs[i].process) idx = i;
+    if (idx < 0) return MG_ERR_BAD_PROCESS;
+    const mg_proc_table *t = &tabs[idx];
+
+    mg_process *p = (mg_process *)calloc(1, sizeof(mg_process));
+    if (!p) return MG_ERR_NO_MEMORY;
+    p->tab = t;
+    p->table_index = idx;
+    p->par = par;
+    p->ngood = -1;
+    p->tpe = default_tpe(t->npar);
+    p->block = 128;
+    const double gs = sqrt(4.0 * M_PI * par.alphas);
+    p->factor = pow(gs, 2 * t->ngluon) / (t->iden * (double)t->denom);
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) {
+        free_proc(p);
+        return cuda_fail(e);
+    }
+    // packed upper triangle of D*C with doubled off-diagonals (exact in FP64)
+    const int nc = t->ncolor;
+    const size_t ntri = (size_t)nc * (nc + 1) / 2;
+    double *cup = (double *)malloc(sizeof(double) * ntri);
+    if (!cup) {
+        free_proc(p);
+        return MG_ERR_NO_MEMORY;
+    }
+    size_t w = 0;
+    for (int i = 0; i < nc; i++)
+        for (int j = i; j < nc; j++) cup[w++] = (i == j ? 1.0 : 2.0) * (double)t->chat[i * nc + j];
+    int st = MG_OK;
+#define TRY(call)                                   \
+    do {                                            \
+        cudaError_t _e = (call);                    \
+        if (_e != cudaSuccess) {                    \
+            st = (_e == cudaErrorMemoryAllocation) ? MG_ERR_NO_MEMORY : cuda_fail(_e); \
+            goto fail;                              \
+        }                                           \
+    } while (0)
+    TRY(cudaMalloc(&p->d_ops, sizeof(int32_t) * 8 * t->nops));
+    TRY(cudaMalloc(&p->d_scat, sizeof(int32_t) * (t->nscat > 0 ? t->nscat : 1)));
+    TRY(cudaMalloc(&p->d_cup, sizeof(double) * ntri));
+    TRY(cudaMalloc(&p->d_hel, sizeof(int) * 256));
+    TRY(cudaMemcpy(p->d_ops, t->ops, sizeof(int32_t) * 8 * t->nops, cudaMemcpyHostToDevice));
+    if (t->nscat > 0)
+        TRY(cudaMemcpy(p->d_scat, t->scat, sizeof(int32_t) * t->nscat, cudaMemcpyHostToDevice));
+    TRY(cudaMemcpy(p->d_cup, cup, sizeof(double) * ntri, cudaMemcpyHostToDevice));
+#undef TRY
+    free(cup);
+    if (par.hel_mode == MG_HEL_ALL) {
+        uint8_t all[256];
+        memset(all, 1, sizeof(all));
+        st = set_hel_list(p, all);
+        if (st != MG_OK) {
+            free_proc(p);
+            return st;
+        }
+    }
+    *out = p;
+    return MG_OK;
+fail:
+    free(cup);
+    free_proc(p);
+    return st;
+}
+
+void mg_process_destroy(mg_process *p) { free_proc(p); }
+
+int mg_process_info(const mg_process *p, mg_info *o) {
+    if (!p || !o) return MG_ERR_BAD_ARG;
+    const mg_proc_table *t = p->tab;
+    o->npar = t->npar;
+    o->ngluon = t->ngluon;
+    o->ndiagrams = t->ndiagrams;
+    o->nterms = t->nterms;
+    o->ncolor = t->ncolor;
+    o->nhel = 1 << t->npar;
+    o->ngood = p->ngood;
+    o->nslot = t->nslot;
+    o->nops = t->nops;
+    o->njamp_updates = t->nscat;
+    o->denom = t->denom;
+    o->iden = t->iden;
+    o->flops_diagram = t->flops_diagram;
+    o->flops_colour = t->flops_colour;
+    return MG_OK;
+}
+
+int mg_color_matrix(const mg_process *p, int64_t *ints_out, int64_t *denom_out) {
+    if (!p || !ints_out) return MG_ERR_BAD_ARG;
+    const int nc = p->tab->ncolor;
+    for (int i = 0; i < nc * nc; i++) ints_out[i] = p->tab->chat[i];
+    if (denom_out) *denom_out = p->tab->denom;
+    return MG_OK;
+}
+
+int mg_helicity_mask(const mg_process *p, uint8_t *mask_out) {
+    if (!p || !mask_out) return MG_ERR_BAD_ARG;
+    if (p->ngood < 0) return MG_ERR_NOT_FILTERED;
+    memcpy(mask_out, p->mask, (size_t)1 << p->tab->npar);
+    return MG_OK;
+}
+
+int mg_set_launch(mg_process *p, int tpe, int block) {
+    if (!p) return MG_ERR_BAD_ARG;
+    if (tpe) {
+        if (tpe < 1 || tpe > 32 || (tpe & (tpe - 1))) return MG_ERR_BAD_ARG;
+        p->tpe = tpe;
+    }
+    if (block) {
+        if (block < 32 || block > 1024 || block % 32) return MG_ERR_BAD_ARG;
+        p->block = block;
+    }
+    return MG_OK;
+}
+
+int mg_filter_helicities(mg_process *p, const double *mom, int64_t n, void *stream, int *ngood_out) {
+    if (!p) return MG_ERR_BAD_ARG;
+    if (n < 1 || n > 65536) return MG_ERR_BAD_ARG;
+    int st = check_dev_ptr(mom, p->device);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nhel = 1 << p->tab->npar;
+    // evaluate every helicity: temporary list 0..nhel-1
+    uint8_t all[256];
+    memset(all, 1, sizeof(all));
+    st = set_hel_list(p, all);
+    if (st) return st;
+    double *mh = nullptr;
+    unsigned char *dmask = nullptr;
+    uint8_t mask[256];
+    cudaError_t e = cudaMalloc(&mh, sizeof(double) * n * nhel);
+    if (e != cudaSuccess) {
+        p->ngood = -1;
+        return e == cudaErrorMemoryAllocation ? MG_ERR_NO_MEMORY : cuda_fail(e);
+    }
+    e = cudaMalloc(&dmask, nhel);
+    if (e == cudaSuccess) e = cudaMemsetAsync(mh, 0, sizeof(double) * n * nhel, s);
+    if (e == cudaSuccess)
+        e = mg_launch_sigmakin(dev_view(p), mom, n, p->d_hel, nhel, 32, p->block, nullptr, mh, s);
+    if (e == cudaSuccess) e = mg_launch_helmask(mh, n, nhel, 1e-14, dmask, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(mask, dmask, nhel, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(mh);
+    cudaFree(dmask);
+    if (e != cudaSuccess) {
+        p->ngood = -1;
+        return cuda_fail(e);
+    }
+    st = set_hel_list(p, mask);
+    if (st) return st;
+    if (ngood_out) *ngood_out = p->ngood;
+    return MG_OK;
+}
+
+static int sigmakin_impl(mg_process *p, const double *mom, int64_t nevt, double *me,
+                         double *me_hel, void *stream) {
+    if (!p) return MG_ERR_BAD_ARG;
+    if (nevt < 0) return MG_ERR_BAD_ARG;
+    if (p->ngood < 0) return MG_ERR_NOT_FILTERED;
+    if (nevt == 0) return MG_OK;
+    int st = check_dev_ptr(mom, p->device);
+    if (st) return st;
+    if (me && (st = check_dev_ptr(me, p->device))) return st;
+    if (me_hel && (st = check_dev_ptr(me_hel, p->device))) return st;
+    if (!me && !me_hel) return MG_ERR_BAD_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nhel = 1 << p->tab->npar;
+    if (me_hel) MG_CUDA(cudaMemsetAsync(me_hel, 0, sizeof(double) * nevt * nhel, s));
+    if (p->ngood == 0) {
+        if (me) MG_CUDA(cudaMemsetAsync(me, 0, sizeof(double) * nevt, s));
+        return MG_OK;
+    }
+    int tpe = p->tpe;
+    while (tpe > 1 && tpe > p->ngood) tpe >>= 1;
+    MG_CUDA(mg_launch_sigmakin(dev_view(p), mom, nevt, p->d_hel, p->ngood, tpe, p->block, me,
+                               me_hel, s));
+    return MG_OK;
+}
+
+int mg_sigmakin(mg_process *p, const double *mom, int64_t nevt, double *me, void *stream) {
+    if (!me) return MG_ERR_BAD_ARG;
+    return sigmakin_impl(p, mom, nevt, me, nullptr, stream);
+}
+
+int mg_sigmakin_hel(mg_process *p, const double *mom, int64_t nevt, double *me, double *me_hel,
+                    void *stream) {
+    if (!me_hel) return MG_ERR_BAD_ARG;
+    return sigmakin_impl(p, mom, nevt, me, me_hel, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,252 @@
+// Diagram kernel: one thread per (event, helicity slot) executes the
+// process's wavefunction/amplitude program (compiler/program.py) and the
+// FP64 colour sum, then the helicity slots of an event are reduced with warp
+// shuffles.
+//
+// Structure of the paper's sigmaKin (Sec. 3): per event and good helicity,
+// external wavefunctions -> internal wavefunctions -> amplitudes -> jamps ->
+// quadratic form J^H C J (Sec. 5, Eq. "jcj", here sum_ij D*C_ij (A_i A_j +
+// B_i B_j) with the symmetric matrix walked as an upper triangle, Sec. 6
+// "triangular" colour sum) -> running sum over helicities.
+//
+// GB300 design notes.  The FP64 pipe is the bottleneck of this kernel by a
+// wide margin, so the program is table driven: an op record is a uniform
+// (warp-broadcast) load, the dispatch is warp-uniform, and wavefunctions,
+// jamps and per-event kinematics live in per-thread local memory.  Per-event
+// quantities (momentum sums, 1/P^2, top propagators) are computed once per
+// thread and reused by all of its helicities.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mg_dirac.cuh"
+#include "mg_internal.h"
+#include "mg_proc_list.h"
+
+using namespace mg;
+
+namespace {
+
+template <int NG>
+struct Kin {
+    static constexpr int NPAR = NG + 2;
+    static constexpr int NS = 1 << NG;
+    double P[NPAR][4];   // momenta as given
+    double K[NS][4];     // sum of incoming momenta of the gluons in subset S
+    double IP2[NS];      // 1 / K_S^2
+    double QP[NS][4];    // top-line momentum after absorbing S from ubar: p3 - K_S
+    cx DP[NS];           // 1 / (QP^2 - m^2 + i m w)
+    double QS[NS][4];    // top-line momentum after absorbing S from v: K_S - p4
+    cx DS[NS];           // 1 / (QS^2 - m^2 + i m w)
+};
+
+__device__ __forceinline__ cx cinv(double a, double b) {
+    const double d = 1.0 / fma(a, a, b * b);
+    return mk(a * d, -b * d);
+}
+
+template <int NG>
+__device__ void kinematics(Kin<NG> &k, const double *__restrict__ p, double mt, double wt) {
+    constexpr int NPAR = NG + 2, NS = 1 << NG;
+#pragma unroll
+    for (int i = 0; i < NPAR; i++)
+#pragma unroll
+        for (int m = 0; m < 4; m++) k.P[i][m] = __ldg(p + 4 * i + m);
+    double Kg[NG][4];
+#pragma unroll
+    for (int g = 0; g < NG; g++) {
+        const int ip = (g < 2) ? g : g + 2;
+        const double sg = (g < 2) ? 1.0 : -1.0;
+#pragma unroll
+        for (int m = 0; m < 4; m++) Kg[g][m] = sg * k.P[ip][m];
+    }
+    const double m2 = mt * mt, mw = mt * wt;
+    for (int m = 0; m < 4; m++) k.K[0][m] = 0.0;
+    k.IP2[0] = 0.0;
+    for (int S = 1; S < NS; S++) {
+        const int low = __ffs(S) - 1;
+        const int rest = S & (S - 1);
+        for (int m = 0; m < 4; m++) k.K[S][m] = k.K[rest][m] + Kg[low][m];
+        const double *K = k.K[S];
+        const double k2 = K[0] * K[0] - K[1] * K[1] - K[2] * K[2] - K[3] * K[3];
+        k.IP2[S] = rest ? 1.0 / k2 : 0.0;
+        double q2 = 0.0, s2 = 0.0;
+        for (int m = 0; m < 4; m++) {
+            k.QP[S][m] = k.P[2][m] - K[m];
+            k.QS[S][m] = K[m] - k.P[3][m];
+            const double g = (m == 0) ? 1.0 : -1.0;
+            q2 += g * k.QP[S][m] * k.QP[S][m];
+            s2 += g * k.QS[S][m] * k.QS[S][m];
+        }
+        k.DP[S] = cinv(q2 - m2, mw);
+        k.DS[S] = cinv(s2 - m2, mw);
+    }
+}
+
+__device__ __forceinline__ int hel_sign(int hel, int npar, int ip) {
+    return ((hel >> (npar - 1 - ip)) & 1) ? 1 : -1;
+}
+
+// Executes the program for one helicity; returns sum_ij D*C_ij Re(J_i^* J_j).
+template <int NG, int NSLOT, int NC>
+__device__ double run_program(const Kin<NG> &k, int hel, const int4 *__restrict__ ops, int nops,
+                              const int *__restrict__ scat, const double *__restrict__ cup,
+                              double mt, cx (*W)[4], cx *J) {
+    constexpr int NPAR = NG + 2;
+    for (int c = 0; c < NC; c++) J[c] = mk(0.0, 0.0);
+    for (int i = 0; i < nops; i++) {
+        const int4 a = __ldg(ops + 2 * i);
+        const int4 b = __ldg(ops + 2 * i + 1);
+        switch (a.x) {
+            case MG_OP_EXT_G:
+                ext_gluon(k.P[a.z], hel_sign(hel, NPAR, a.z), a.w != 0, W[a.y]);
+                break;
+            case MG_OP_EXT_UB:
+                ext_ubar(k.P[2], hel_sign(hel, NPAR, 2), W[a.y]);
+                break;
+            case MG_OP_EXT_V:
+                ext_v(k.P[3], hel_sign(hel, NPAR, 3), W[a.y]);
+                break;
+            case MG_OP_V3:
+                vvv_current(W[a.z], k.K[b.x], W[a.w], k.K[b.y], k.IP2[b.x | b.y], W[a.y]);
+                break;
+            case MG_OP_V4:
+                vvvv_currents(W[b.x], W[b.y], W[b.z], k.IP2[b.w], W[a.y], W[a.z], W[a.w]);
+                break;
+            case MG_OP_FPRE: {
+                const Slash s = slash_blocks(W[a.w]);
+                cx t[4], o[4];
+                row_slash(W[a.z], s, t);
+                row_qm(t, k.QP[b.x], mt, o);
+                const cx d = k.DP[b.x];
+                for (int m = 0; m < 4; m++) W[a.y][m] = o[m] * d;
+                break;
+            }
+            case MG_OP_FSUF: {
+                const Slash s = slash_blocks(W[a.w]);
+                cx t[4], o[4];
+                slash_col(s, W[a.z], t);
+                qm_col(k.QS[b.x], mt, t, o);
+                const cx d = k.DS[b.x];
+                for (int m = 0; m < 4; m++) W[a.y][m] = o[m] * d;
+                break;
+            }
+            case MG_OP_XROW: {
+                const Slash s = slash_blocks(W[a.w]);
+                row_slash(W[a.z], s, W[a.y]);
+                break;
+            }
+            case MG_OP_YCOL: {
+                const Slash s = slash_blocks(W[a.z]);
+                slash_col(s, W[a.w], W[a.y]);
+                break;
+            }
+            case MG_OP_BIL:
+                bilinear(W[a.z], W[a.w], W[a.y]);
+                break;
+            case MG_OP_AMP_SS:
+            case MG_OP_AMP_VV: {
+                const cx amp = (a.x == MG_OP_AMP_SS) ? sdot(W[a.z], W[a.w]) : mdot(W[a.z], W[a.w]);
+                const int end = b.x + b.y;
+                for (int s = b.x; s < end; s++) {
+                    const int e = __ldg(scat + s);
+                    const int j = e >> 2;
+                    switch (e & 3) {
+                        case 0: J[j] = J[j] + amp; break;
+                        case 1: J[j] = J[j] - amp; break;
+                        case 2: J[j] = J[j] + mk(-amp.i, amp.r); break;
+                        default: J[j] = J[j] + mk(amp.i, -amp.r); break;
+                    }
+                }
+                break;
+            }
+            default:
+                break;
+        }
+    }
+    // colour sum over the packed upper triangle (diagonal D*C_ii,
+    // off-diagonal 2*D*C_ij): sum_i A_i z_i + B_i y_i
+    double me = 0.0;
+    const double *c = cup;
+    for (int i = 0; i < NC; i++) {
+        double zr = 0.0, zi = 0.0;
+        for (int j = i; j < NC; j++) {
+            const double cij = __ldg(c++);
+            zr = fma(cij, J[j].r, zr);
+            zi = fma(cij, J[j].i, zi);
+        }
+        me = fma(J[i].r, zr, fma(J[i].i, zi, me));
+    }
+    return me;
+}
+
+template <int NG, int NSLOT, int NC>
+__global__ void __launch_bounds__(256)
+    k_sigmakin(const double *__restrict__ mom, long long nevt, const int4 *__restrict__ ops,
+               int nops, const int *__restrict__ scat, const double *__restrict__ cup,
+               const int *__restrict__ hel, int ngood, int tpe, double mt, double wt,
+               double factor, double *__restrict__ me, double *__restrict__ me_hel) {
+    constexpr int NPAR = NG + 2;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long e = t / tpe;
+    const int s = (int)(t - e * tpe);
+    double sum = 0.0;
+    if (e < nevt) {
+        Kin<NG> k;
+        kinematics<NG>(k, mom + e * (NPAR * 4), mt, wt);
+        cx W[NSLOT][4];
+        cx J[NC];
+        for (int ih = s; ih < ngood; ih += tpe) {
+            const int h = __ldg(hel + ih);
+            const double mh = run_program<NG, NSLOT, NC>(k, h, ops, nops, scat, cup, mt, W, J);
+            if (me_hel) me_hel[e * (1LL << NPAR) + h] = mh * factor;
+            sum += mh;
+        }
+    }
+    for (int o = tpe >> 1; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (e < nevt && s == 0 && me) me[e] = sum * factor;
+}
+
+// Helicity filter rule: good[h] = any_e ( mh[e][h] > rel * max_h' mh[e][h'] ).
+__global__ void k_helmask(const double *__restrict__ mh, long long n, int nhel, double rel,
+                          unsigned char *__restrict__ mask) {
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= nhel) return;
+    unsigned char good = 0;
+    for (long long e = 0; e < n; e++) {
+        const double *row = mh + e * nhel;
+        double mx = 0.0;
+        for (int j = 0; j < nhel; j++) mx = fmax(mx, row[j]);
+        if (row[h] > rel * mx) good = 1;
+    }
+    mask[h] = good;
+}
+
+}  // namespace
+
+cudaError_t mg_launch_sigmakin(const mg_dev_proc &dp, const double *mom, int64_t nevt,
+                               const int *hel_list, int ngood, int tpe, int block, double *me,
+                               double *me_hel, cudaStream_t stream) {
+    if (nevt <= 0) return cudaSuccess;
+    const long long threads = (long long)nevt * tpe;
+    const long long grid = (threads + block - 1) / block;
+    if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
+    switch (dp.table_index) {
+#define MG_LAUNCH(IDX, NG, NSLOT, NC)                                                            \
+    case IDX:                                                                                    \
+        k_sigmakin<NG, NSLOT, NC><<<(unsigned)grid, block, 0, stream>>>(                         \
+            mom, nevt, reinterpret_cast<const int4 *>(dp.ops), dp.nops, dp.scat, dp.cup, hel_list, \
+            ngood, tpe, dp.mt, dp.wt, dp.factor, me, me_hel);                                    \
+        break;
+        MG_PROC_LIST(MG_LAUNCH)
+#undef MG_LAUNCH
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t mg_launch_helmask(const double *me_hel, int64_t n, int nhel, double rel,
+                              unsigned char *mask, cudaStream_t stream) {
+    k_helmask<<<(nhel + 127) / 128, 128, 0, stream>>>(me_hel, n, nhel, rel, mask);
+    return cudaGetLastError();
+}

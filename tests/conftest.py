@@ -11,3 +11,12 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: long-running CPU test")
+
+
+@pytest.fixture(scope="session", autouse=True)
+def _built_library():
+    """Compile the oracle and the CUDA library once per test session."""
+    import oracle
+    from paper_2510_05392_gb300 import build
+    oracle.build()
+    build.build()

@@ -1,0 +1,107 @@
+"""Process compiler and C-ABI library checks that need no GPU."""
+import ctypes
+import json
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import color as ocolor
+from paper_2510_05392_gb300 import phasespace as ps
+from paper_2510_05392_gb300.compiler import colour, diagrams, program
+
+import table_emulator
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+GOLDEN = os.path.join(ROOT, "tests", "golden", "paper_table_complexity.json")
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5])
+def test_diagram_counts_match_paper(n):
+    g = json.load(open(GOLDEN))["processes"]
+    proc = "g g > t t~" + " g" * (n - 2)
+    P = diagrams.Process(n)
+    assert P.ndiagrams == g[proc]["diagrams"]
+    # every colour coefficient of every diagram term is +-1 or +-i and every
+    # string is a permutation of the gluons
+    for d in P.diagrams:
+        for s, c in d.color.items():
+            assert sorted(s) == list(range(n))
+            assert complex(c) in (1, -1, 1j, -1j)
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 6])
+def test_colour_matrix_bit_exact_vs_oracle(n):
+    a = colour.colour_matrix(n)
+    b = ocolor.color_matrix(n)
+    assert a[1] == b[1]
+    assert a[0] == b[0]
+    assert [tuple(x) for x in a[2]] == [tuple(x) for x in b[2]]
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5])
+def test_program_slots_well_formed(n):
+    prog = program.build_program(n)
+    written = set()
+    for r in prog.ops:
+        c = r[0]
+        ins = {program.OP_V3: r[2:4], program.OP_V4: r[4:7], program.OP_FPRE: r[2:4],
+               program.OP_FSUF: r[2:4], program.OP_XROW: r[2:4], program.OP_YCOL: r[2:4],
+               program.OP_BIL: r[2:4], program.OP_AMP_SS: r[2:4],
+               program.OP_AMP_VV: r[2:4]}.get(c, [])
+        outs = {program.OP_V4: r[1:4]}.get(c, [r[1]] if c not in (program.OP_AMP_SS, program.OP_AMP_VV) else [])
+        for s in ins:
+            assert s in written
+        for s in outs:
+            assert 0 <= s < prog.nslot
+            assert s not in ins
+        written.update(outs)
+    assert all(0 <= (e >> 2) < prog.ncolor for e in prog.scatter)
+
+
+@pytest.mark.parametrize("ng", [0, 1, 2])
+def test_compiled_tables_match_oracle_on_cpu(ng):
+    """The op tables, executed by a numpy restatement of their semantics,
+    reproduce the oracle per helicity (validates the compiler, not CUDA)."""
+    p = ps.generate(5, ng, 1500.0, 900 + ng, ptmin=20.0, drmin=0.4) if ng else \
+        ps.generate(5, 0, 1000.0, 900)
+    a, ah = table_emulator.run(ng + 2, p, per_helicity=True)
+    b, bh = oracle.me(p, per_helicity=True)
+    assert np.abs(a / b - 1).max() < 1e-12
+    assert np.abs(ah - bh).max() < 1e-12 * bh.max()
+
+
+# ----------------------------------------------------------- C ABI -------
+
+def _header_functions():
+    txt = open(os.path.join(ROOT, "include", "mgpu.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(mg_[a-z_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2510_05392_gb300 import binding
+    L = binding.lib()
+    names = _header_functions()
+    assert len(names) >= 11
+    for name in names:
+        assert hasattr(L, name), name
+
+
+def test_status_strings_without_gpu():
+    from paper_2510_05392_gb300 import binding
+    L = binding.lib()
+    assert L.mg_status_string(0) == b"ok"
+    assert L.mg_status_string(-1) == b"unknown or unsupported process"
+    assert L.mg_status_string(-3) == b"helicities not filtered"
+
+
+def test_null_arguments_rejected_without_gpu():
+    from paper_2510_05392_gb300 import binding
+    L = binding.lib()
+    h = ctypes.c_void_p()
+    assert L.mg_process_create(None, None, ctypes.byref(h)) == binding.MG_ERR_BAD_ARG
+    assert L.mg_sigmakin(None, None, 1, None, None) == binding.MG_ERR_BAD_ARG
+    assert L.mg_process_info(None, None) == binding.MG_ERR_BAD_ARG

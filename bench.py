@@ -1,0 +1,338 @@
+"""Throughput benchmark: g g -> t t~ g g matrix elements on GB300.
+
+Workload (default): 524288 synthetic events of g g -> t t~ g g at sqrt(s) =
+1500 GeV with gluon cuts (pT > 20 GeV, Delta R > 0.4), FP64 path, inputs
+resident in HBM.  One step = one mg_sigmakin call over the whole batch
+(momentum read, diagrams, colour sum, helicity sum).
+
+Prints one JSON line (rank 0).  Keys beyond the basic ones:
+  e2e          the same metric through the public API with pinned host
+               buffers: H2D of the step's momenta + mg_sigmakin + D2H of the
+               matrix elements, every step
+  roofline     the diagram kernel against the FP64 pipe ("alu"): algorithmic
+               FP64 flops per launch / CUDA-event launch time vs the FP64 FMA
+               peak measured live by mg_probe_fp64_peak
+  cpu_baseline the CPU oracle on the host cores on a bounded sample
+  clocks       nvidia-smi samples taken during the timed region
+
+--impl reference times the CPU oracle (the only reference this workload
+has) on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ME events/s per process on 1 GB300: FP64 vs mixed vs surrogate; % of FP64 peak"
+WORKLOADS = {
+    # name: (process, ngluon_final, nevt, sqrt_s, cuts, seed)
+    "ggttgg_524288": ("g g > t t~ g g", 2, 524288, 1500.0, True, 20251005 + 2),
+    "ggtt_16384": ("g g > t t~", 0, 16384, 1000.0, False, 20251005 + 1),
+    "ggttggg_262144": ("g g > t t~ g g g", 3, 262144, 1500.0, True, 20251005 + 3),
+}
+TEST_SEED = 12345  # helicity-filter test events
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _events(name, nevt=None, first_candidate=0):
+    from paper_2510_05392_gb300 import phasespace as ps
+    proc, ng, n, sqrts, cuts, seed = WORKLOADS[name]
+    kw = dict(ptmin=20.0, drmin=0.4) if cuts else {}
+    return ps.generate(nevt or n, ng, sqrts, seed, first_candidate=first_candidate, **kw)
+
+
+def _test_events(name):
+    from paper_2510_05392_gb300 import phasespace as ps
+    proc, ng, n, sqrts, cuts, seed = WORKLOADS[name]
+    kw = dict(ptmin=20.0, drmin=0.4) if cuts else {}
+    return ps.generate(16, ng, sqrts, TEST_SEED, **kw)
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(gpu_index)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    for f in ["mg_kernels.cu", "mg_dirac.cuh", "mg_internal.h"]:
+        with open(os.path.join(ROOT, "paper_2510_05392_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel, workload):
+    """DRAM bytes per launch from the committed ncu summary, when it was
+    taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        data = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    e = data.get(f"{kernel}:{workload}")
+    if not e or e.get("kernel_hash") != _kernel_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def cpu_baseline(name, nsample, steps=1):
+    """The oracle (as it stands) on the host cores over the first nsample
+    events of the workload; returns (events/s, threads, seconds)."""
+    import oracle
+    mom = _events(name, nsample)
+    oracle.me(mom[:8])  # load/compile, warm
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        oracle.me(mom)
+    dt = time.perf_counter() - t0
+    return steps * nsample / dt, oracle.threads(), dt
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    name = args.workload
+    n = args.ref_sample
+    import oracle
+    mom = _events(name, n)
+    oracle.me(mom[:8])
+    for _ in range(args.warmup):
+        oracle.me(mom[: max(1, n // 8)])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.me(mom)
+    dt = time.perf_counter() - t0
+    value = args.steps * n / dt
+    proc = WORKLOADS[name][0]
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "events/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": name, "process": proc, "nevt_per_step": n,
+                   "sample": f"first {n} events of {name}"},
+        "cpu_baseline": {"value": value, "unit": "events/s", "cores": oracle.threads(),
+                         "kind": "oracle", "sample": f"first {n} events of {name} per step"},
+        "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    from paper_2510_05392_gb300 import binding, build
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    build.build()
+    name = args.workload
+    proc, ng, n_default, sqrts, cuts, seed = WORKLOADS[name]
+    nevt = args.nevt or n_default
+    npar = ng + 4
+    # each rank evaluates its own nevt events (weak scaling; rank 0 holds the
+    # standard workload, rank r the next candidates of the same generator)
+    mom_h = _events(name, nevt, first_candidate=rank * (1 << 40))
+    mom = torch.from_numpy(mom_h).to(dev)
+    out = torch.empty(nevt, dtype=torch.float64, device=dev)
+    p = binding.Process(proc)
+    ngood = p.filter_helicities(torch.from_numpy(_test_events(name)).to(dev))
+    if args.tpe or args.block:
+        p.set_launch(args.tpe, args.block)
+    info = p.info()
+    stream = torch.cuda.current_stream(dev)
+
+    # FP64 peak measured live on this GPU (roofline denominator)
+    L = binding.lib()
+    L.mg_probe_fp64_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.POINTER(ctypes.c_double)]
+    peak = ctypes.c_double(0.0)
+    rc = L.mg_probe_fp64_peak(0, 20000, 5, ctypes.byref(peak))
+    fp64_peak = peak.value if rc == 0 else None
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    for _ in range(args.warmup):
+        p.sigmakin(mom, out, stream)
+    torch.cuda.synchronize(dev)
+
+    clocks = Clocks(local) if (rank == 0 and not args.no_clocks) else None
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)  # L2 flush between timed launches (not timed)
+        ev[i][0].record(stream)
+        p.sigmakin(mom, out, stream)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t0
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop() if clocks else None
+    launch_ms = [a.elapsed_time(b) for a, b in ev]
+    t_dev = sum(launch_ms) / 1e3
+    if ws > 1:
+        tt = torch.tensor([t_dev], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_dev = tt.item()
+    value = ws * nevt * args.steps / t_dev
+    ms_step = 1e3 * t_dev / args.steps
+
+    # algorithmic FP64 work of one launch
+    flops_launch = nevt * ngood * (info.flops_diagram + info.flops_colour)
+    achieved = flops_launch / (statistics.mean(launch_ms) / 1e3)
+
+    # end to end through the public API with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        host_in = torch.from_numpy(mom_h).pin_memory()
+        host_out = torch.empty(nevt, dtype=torch.float64).pin_memory()
+        for _ in range(1):
+            mom.copy_(host_in, non_blocking=True)
+            p.sigmakin(mom, out, stream)
+            host_out.copy_(out, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            torch.distributed.barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            mom.copy_(host_in, non_blocking=True)
+            p.sigmakin(mom, out, stream)
+            host_out.copy_(out, non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        te = a.elapsed_time(b) / 1e3
+        if ws > 1:
+            tt = torch.tensor([te], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            te = tt.item()
+        e2e = {"value": ws * nevt * args.steps / te, "unit": "events/s",
+               "h2d_bytes_per_step": nevt * npar * 4 * 8, "d2h_bytes_per_step": nevt * 8}
+        assert torch.isfinite(host_out).all().item()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, cores, dt = cpu_baseline(name, args.cpu_sample)
+        cpu = {"value": v, "unit": "events/s", "cores": cores, "kind": "oracle",
+               "sample": f"first {args.cpu_sample} events of {name}, {dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic (Philox4x32-10 + massive RAMBO, gluon cuts)",
+            "config": {"workload": name, "process": proc, "nevt_per_gpu": nevt,
+                       "sqrt_s_gev": sqrts, "cuts": "pT>20 GeV, dR>0.4 (final gluons)" if cuts else "none",
+                       "precision": "fp64", "ngood_helicities": ngood,
+                       "l2": "flushed between timed launches (256 MiB write, untimed)",
+                       "parallelism": f"dp{ws} (independent events per GPU)"},
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12,
+                         "peak": fp64_peak / 1e12 if fp64_peak else None,
+                         "unit": "TFLOP/s",
+                         "frac": achieved / fp64_peak if fp64_peak else None,
+                         "traffic": _traffic("k_sigmakin", f"{name}"),
+                         "kernel": "k_sigmakin (FP64 pipe; peak = FP64 FMA probe, measured live)",
+                         "flops_per_launch": flops_launch},
+            "e2e": e2e,
+            "gpu_launches": args.steps,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+            "wall_s_timed": wall,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="ggttgg_524288", choices=sorted(WORKLOADS))
+    ap.add_argument("--nevt", type=int, default=0, help="override events per GPU (profiling)")
+    ap.add_argument("--tpe", type=int, default=0)
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--cpu-sample", type=int, default=16384)
+    ap.add_argument("--ref-sample", type=int, default=4096)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours" and not args.nevt:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

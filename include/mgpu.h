@@ -3,12 +3,12 @@
  * NVIDIA GB300 (sm_103a).  C ABI.
  *
  * What the library computes is the per-event matrix element engine of the
- * paper (Sec. 3, "sigmaKin": input 4*npar doubles per event, output one
+ * paper (Sec. 2.2, "sigmaKin": input 4*npar doubles per event, output one
  * matrix element per event): external wavefunctions, internal wavefunctions
  * and amplitudes of every Feynman diagram, accumulated into colour-flow
- * amplitudes ("jamps"), contracted with the colour matrix (Sec. 5, Eq. "jcj":
+ * amplitudes ("jamps"), contracted with the colour matrix (Sec. 3.3, Eq. "jcj":
  * J^H C J = A^T C A + B^T C B with J = A + iB), summed over the good
- * helicities (Sec. 3 and Sec. 8, helicity filtering) and averaged over
+ * helicities (Sec. 2.2 and Sec. 4.6, helicity filtering) and averaged over
  * initial spins/colours and identical final gluons.
  *
  * Conventions
@@ -89,7 +89,7 @@ typedef struct {
  * alphas 0.118, filtered helicities, FP64). */
 int mg_process_create(const char *process, const mg_params *params, mg_process **out);
 
-/* Helicity filter (Sec. 3 and Sec. 8 of the paper: keep the helicities with
+/* Helicity filter (Sec. 2.2 and Sec. 4.6 of the paper: keep the helicities with
  * a non-zero contribution).  Evaluates all 2^npar helicities in parallel on
  * the n test events momenta_dev[n][npar][4] and keeps h when
  * |M_h|^2 > 1e-14 * max_h' |M_h'|^2 on any of them.  Synchronises the stream
@@ -98,7 +98,8 @@ int mg_filter_helicities(mg_process *p, const double *momenta_dev, int64_t n, vo
                          int *ngood_out);
 
 /* Matrix elements of nevt events: me_out_dev[nevt] (float64, device).
- * nevt = 0 is a no-op.  Asynchronous on stream.  Requires a prior
+ * nevt = 0 is a no-op (the pointers are then not inspected and may be
+ * NULL).  Asynchronous on stream.  Requires a prior
  * mg_filter_helicities unless hel_mode == MG_HEL_ALL.  Non-finite momenta
  * give non-finite results (not checked). */
 int mg_sigmakin(mg_process *p, const double *momenta_dev, int64_t nevt, double *me_out_dev,

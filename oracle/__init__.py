@@ -149,7 +149,7 @@ def amplitudes(p_event: np.ndarray, hel: int, gauge_leg: int = -1,
 def good_helicity_mask(momenta_test: np.ndarray, rel: float = 1e-14, **kw) -> np.ndarray:
     """Helicity filter rule: h is good when |M_h|^2 > rel * max_h' |M_h'|^2 on
     any of the test events (the paper keeps the helicities with a non-zero
-    contribution, Sec. 3 and Sec. 8, without stating a threshold)."""
+    contribution, Sec. 2.2 and Sec. 4.6, without stating a threshold)."""
     _, mh = me(momenta_test, per_helicity=True, **kw)
     mx = mh.max(axis=1, keepdims=True)
     return (mh > rel * mx).any(axis=0).astype(np.uint8)

@@ -11,10 +11,10 @@
  * the top line, C_st = Tr((T^s)^dagger T^t) the colour matrix (exact rational,
  * built by oracle/color.py and passed in), and h all helicity combinations.
  * This is the colour-flow/quadratic-form structure of the paper's colour sum
- * (Sec. 5, Eq. "jcj": J^H C J with C real symmetric), evaluated here by a
+ * (Sec. 3.3, Eq. "jcj": J^H C J with C real symmetric), evaluated here by a
  * different algorithm than the Feynman-diagram method: the colour-ordered
- * amplitudes come from Berends-Giele recursion, which the paper's outlook
- * (Sec. 8) names as the better approach for many gluons.
+ * amplitudes come from Berends-Giele recursion, which the paper
+ * (Sec. 4.5) names as the better approach for many gluons.
  *
  * Conventions (textbook QCD, metric +---, Tr(t^a t^b) = delta^ab / 2):
  *   quark-gluon vertex  i g gamma^mu t^a

@@ -8,7 +8,7 @@ form of Ellis, Stirling, Webber, "QCD and collider physics", eq. (10.12):
 with t1 = 2 p1.p3 / s, t2 = 2 p2.p3 / s, rho = 4 m^2 / s, averaged over the
 initial spins and colours and summed over the final ones.  It is the n = 2
 case of the matrix element the paper computes (its smallest process, g g ->
-t t~, Sec. 2), at zero top width.
+t t~, table "complexity"), at zero top width.
 """
 from __future__ import annotations
 

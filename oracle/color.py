@@ -3,7 +3,7 @@
 Only tests/, the smoke check and the benchmark's CPU-baseline leg use this
 module.  It shares nothing with the CUDA path's own colour builder.
 
-Definition (the paper's colour sum, Sec. 5, Eq. "jcj": |M|^2 = J^H C J with a
+Definition (the paper's colour sum, Sec. 3.3, Eq. "jcj": |M|^2 = J^H C J with a
 real symmetric colour matrix C over the colour flows):
 for the single top line with n gluons, the flows are the strings
 (t^{a_s1} ... t^{a_sn})_{i j} for all orderings s of the gluons, and

@@ -1,8 +1,8 @@
 """Brute-force count of tree Feynman diagrams for g g -> t t~ + (n-2) g (oracle).
 
 Test infrastructure only; independent of the process compiler's own diagram
-generator.  The paper's process-complexity table (Sec. 2, table
-"complexity", row "Feynman diagrams") gives 3 / 16 / 123 / 1240 / 15495
+generator.  The paper's process-complexity table (table "complexity" in
+Sec. 3, row "Feynman diagrams") gives 3 / 16 / 123 / 1240 / 15495
 diagrams for 2 to 6 gluons, each 4-gluon vertex counted once.
 
 Method: every unrooted tree with labelled leaves and internal vertices of

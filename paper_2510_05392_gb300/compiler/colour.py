@@ -1,7 +1,7 @@
 """Exact colour matrix for the CUDA path's colour sum.
 
 The paper's colour sum is the quadratic form J^H C J over the colour flows
-(Sec. 5, Eq. "jcj"), with C real and symmetric.  For one top line and n
+(Sec. 3.3, Eq. "jcj"), with C real and symmetric.  For one top line and n
 gluons the flows are the generator strings (t^{a_s1}...t^{a_sn})_{ij}, and
 C_st = sum over colours of Tr(t^{a_sn}...t^{a_s1} t^{a_t1}...t^{a_tn}).
 

@@ -1,8 +1,8 @@
 """Feynman diagrams of g g -> t t~ + (n-2) g with full-colour QCD vertices.
 
 This is the "Feynman diagrams -> wavefunctions -> amplitudes -> jamps" half of
-the paper's method (Sec. 3, the sigmaKin / calculate_wavefunctions structure;
-Sec. 7 on diagram groups).  Every tree diagram is a top line (ubar(p3) ...
+the paper's method (Sec. 2.2, the sigmaKin / calculate_wavefunctions
+structure; Sec. 4.2-4.3 on diagram groups).  Every tree diagram is a top line (ubar(p3) ...
 v(p4)) with an ordered sequence of gluon sub-trees attached to it; gluon
 sub-trees are built from 3- and 4-gluon vertices.  Sub-trees ("internal
 wavefunctions") are shared between diagrams, as in HELAS/ALOHA.

@@ -2,8 +2,8 @@
 
 The program is a flat list of operations over numbered wavefunction slots,
 the form in which the CUDA diagram kernel executes it (one table entry per
-HELAS-like call, Sec. 3 of the paper: external wavefunctions, internal
-wavefunctions, amplitudes, jamp updates).  Diagram groups (Sec. 7, "dpg")
+HELAS-like call, Sec. 2.2 of the paper: external wavefunctions, internal
+wavefunctions, amplitudes, jamp updates).  Diagram groups (Sec. 4.2, "dpg")
 are contiguous ranges of the amplitude list.
 
 Closing a diagram.  A diagram term with attachments B1..Bk along the top line

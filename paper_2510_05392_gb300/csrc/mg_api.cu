@@ -337,12 +337,14 @@ static int sigmakin_impl(mg_process *p, const double *mom, int64_t nevt, double 
 }
 
 int mg_sigmakin(mg_process *p, const double *mom, int64_t nevt, double *me, void *stream) {
+    if (p && nevt == 0 && p->ngood >= 0) return MG_OK;
     if (!me) return MG_ERR_BAD_ARG;
     return sigmakin_impl(p, mom, nevt, me, nullptr, stream);
 }
 
 int mg_sigmakin_hel(mg_process *p, const double *mom, int64_t nevt, double *me, double *me_hel,
                     void *stream) {
+    if (p && nevt == 0 && p->ngood >= 0) return MG_OK;
     if (!me_hel) return MG_ERR_BAD_ARG;
     return sigmakin_impl(p, mom, nevt, me, me_hel, stream);
 }

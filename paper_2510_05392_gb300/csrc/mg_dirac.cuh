@@ -1,8 +1,8 @@
 // Device building blocks of the Feynman-diagram calculation: external
-// wavefunctions (the roles of the paper's vxxxxx / ixxxxx / oxxxxx, Sec. 3),
+// wavefunctions (the roles of the paper's vxxxxx / ixxxxx / oxxxxx, Sec. 2.2),
 // gluon currents through the 3- and 4-gluon vertices, top-line
 // wavefunctions with propagators, and amplitude contractions (the roles of
-// the ALOHA routines VVV1P0_1, FFV1_0, ... named in Sec. 3).
+// the ALOHA routines VVV1P0_1, FFV1_0, ... named in Sec. 2.2).
 //
 // Dirac algebra in the chiral representation, 2x2 blocks:
 //   gamma^mu = [[0, sigma^mu], [sigmabar^mu, 0]],

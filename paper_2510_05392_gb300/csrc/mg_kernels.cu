@@ -3,10 +3,10 @@
 // FP64 colour sum, then the helicity slots of an event are reduced with warp
 // shuffles.
 //
-// Structure of the paper's sigmaKin (Sec. 3): per event and good helicity,
+// Structure of the paper's sigmaKin (Sec. 2.2): per event and good helicity,
 // external wavefunctions -> internal wavefunctions -> amplitudes -> jamps ->
-// quadratic form J^H C J (Sec. 5, Eq. "jcj", here sum_ij D*C_ij (A_i A_j +
-// B_i B_j) with the symmetric matrix walked as an upper triangle, Sec. 6
+// quadratic form J^H C J (Sec. 3.3, Eq. "jcj", here sum_ij D*C_ij (A_i A_j +
+// B_i B_j) with the symmetric matrix walked as an upper triangle, Sec. 3.3-3.4
 // "triangular" colour sum) -> running sum over helicities.
 //
 // GB300 design notes.  The FP64 pipe is the bottleneck of this kernel by a

@@ -22,7 +22,7 @@ Generator chain (all vectorised numpy, deterministic for a given seed):
 Particle order in the output is (g1, g2, t, t~, g5, ..., g_npar), with the two
 beams along +z and -z, momenta (E, px, py, pz) in GeV, layout [nevt][npar][4]
 float64.  The paper's own standalone application draws random momenta in the
-same data-parallel way (Sec. 3, "check.exe"), but states no generator, energy
+same data-parallel way (Sec. 2.1-2.2, "check.exe"), but states no generator, energy
 or seed; the choices here are this project's.
 """
 from __future__ import annotations

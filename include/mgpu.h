@@ -97,6 +97,21 @@ int mg_process_create(const char *process, const mg_params *params, mg_process *
 int mg_filter_helicities(mg_process *p, const double *momenta_dev, int64_t n, void *stream,
                          int *ngood_out);
 
+/* Same rule and result as mg_filter_helicities, without allocating device
+ * memory.  The paper has no counterpart; it exists for callers that cannot
+ * call cudaMalloc/cudaFree: code whose device memory is owned by another
+ * allocator (a framework's caching allocator, a fixed memory budget), and
+ * code that must not trigger the device-wide synchronisation of cudaFree
+ * while other streams run.  Its scratch is a fixed 128.25 KiB array inside the
+ * library (held on every GPU that loads it until exit), so n is limited to
+ * 1..64 test events (larger n: MG_ERR_BAD_ARG).  The first call on a device
+ * looks up the array's device address (make it before any stream capture);
+ * the current device must be the process's device.  All calls share the
+ * array: calls whose work overlaps on the GPU (other threads, other streams)
+ * race and must be serialised by the caller.  Synchronises the stream. */
+int mg_filter_helicities_noalloc(mg_process *p, const double *momenta_dev, int64_t n, void *stream,
+                                 int *ngood_out);
+
 /* Matrix elements of nevt events: me_out_dev[nevt] (float64, device).
  * nevt = 0 is a no-op (the pointers are then not inspected and may be
  * NULL).  Asynchronous on stream.  Requires a prior

@@ -7,6 +7,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
 #include <string>
 
 #include "mg_internal.h"
@@ -350,3 +351,76 @@ int mg_sigmakin_hel(mg_process *p, const double *mom, int64_t nevt, double *me, 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Helicity filter without device allocations.
+//
+// mg_filter_helicities allocates (cudaMalloc) and frees (cudaFree, which
+// synchronises the whole device) a scratch buffer on every call.  The variant
+// below takes that scratch from a fixed array compiled into the library
+// instead: room for MG_NOALLOC_FILTER_MAX_EVENTS test events x 256 helicities
+// of |M_h|^2 (FP64) plus a 256-byte mask, 128.25 KiB in total, held on every
+// GPU that loads the library until the process exits.
+#define MG_NOALLOC_FILTER_MAX_EVENTS 64
+#define MG_NOALLOC_MAX_DEVICES 64
+static __device__ __align__(256) unsigned char
+    g_filter_scratch[MG_NOALLOC_FILTER_MAX_EVENTS * 256 * sizeof(double) + 256];
+
+namespace {
+std::mutex g_scratch_mu;
+void *g_scratch_addr[MG_NOALLOC_MAX_DEVICES];  // device address of g_filter_scratch, per device
+
+// Device address of the scratch array on the current device.  The host-side
+// name g_filter_scratch is only a stand-in; kernels must get this address.
+int scratch_address(int device, void **out) {
+    if (device < 0 || device >= MG_NOALLOC_MAX_DEVICES) return MG_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (!g_scratch_addr[device]) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_filter_scratch);
+        if (e != cudaSuccess) return cuda_fail(e);
+        g_scratch_addr[device] = ptr;
+    }
+    *out = g_scratch_addr[device];
+    return MG_OK;
+}
+}  // namespace
+
+extern "C" int mg_filter_helicities_noalloc(mg_process *p, const double *mom, int64_t n,
+                                            void *stream, int *ngood_out) {
+    if (!p) return MG_ERR_BAD_ARG;
+    if (n < 1 || n > MG_NOALLOC_FILTER_MAX_EVENTS) return MG_ERR_BAD_ARG;
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return MG_ERR_CUDA;
+    if (cur != p->device) return MG_ERR_BAD_ARG;
+    int st = check_dev_ptr(mom, p->device);
+    if (st) return st;
+    void *scratch = nullptr;
+    st = scratch_address(cur, &scratch);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nhel = 1 << p->tab->npar;
+    double *mh = (double *)scratch;
+    unsigned char *dmask = (unsigned char *)scratch + MG_NOALLOC_FILTER_MAX_EVENTS * 256 * sizeof(double);
+    uint8_t all[256];
+    memset(all, 1, sizeof(all));
+    st = set_hel_list(p, all);
+    if (st) return st;
+    uint8_t mask[256];
+    // the array keeps the previous call's contents: clear what is read
+    cudaError_t e = cudaMemsetAsync(mh, 0, sizeof(double) * n * nhel, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dmask, 0, nhel, s);
+    if (e == cudaSuccess)
+        e = mg_launch_sigmakin(dev_view(p), mom, n, p->d_hel, nhel, 32, p->block, nullptr, mh, s);
+    if (e == cudaSuccess) e = mg_launch_helmask(mh, n, nhel, 1e-14, dmask, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(mask, dmask, nhel, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        p->ngood = -1;
+        return cuda_fail(e);
+    }
+    st = set_hel_list(p, mask);
+    if (st) return st;
+    if (ngood_out) *ngood_out = p->ngood;
+    return MG_OK;
+}

@@ -74,7 +74,8 @@ typedef struct {
     int ncolor;           /* colour flows                                 */
     int nhel;             /* 2^npar helicity combinations                 */
     int ngood;            /* good helicities (-1 before filtering)        */
-    int nslot;            /* wavefunction slots per thread                */
+    int nslot;            /* gluon-wavefunction slots per thread (1 variant) */
+    int nslot_top;        /* top-line slots per thread (2 helicity variants) */
     int nops;             /* wavefunction/amplitude operations            */
     int njamp_updates;    /* jamp updates per helicity                    */
     int64_t denom;        /* colour-matrix common denominator D           */

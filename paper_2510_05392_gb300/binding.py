@@ -33,7 +33,8 @@ class mg_params(ctypes.Structure):
 class mg_info(ctypes.Structure):
     _fields_ = [("npar", ctypes.c_int), ("ngluon", ctypes.c_int), ("ndiagrams", ctypes.c_int),
                 ("nterms", ctypes.c_int), ("ncolor", ctypes.c_int), ("nhel", ctypes.c_int),
-                ("ngood", ctypes.c_int), ("nslot", ctypes.c_int), ("nops", ctypes.c_int),
+                ("ngood", ctypes.c_int), ("nslot", ctypes.c_int), ("nslot_top", ctypes.c_int),
+                ("nops", ctypes.c_int),
                 ("njamp_updates", ctypes.c_int), ("denom", ctypes.c_int64),
                 ("iden", ctypes.c_double), ("flops_diagram", ctypes.c_double),
                 ("flops_colour", ctypes.c_double)]

@@ -24,44 +24,50 @@ PROCESSES = [
     ("ggttgggg", "g g > t t~ g g g g"),
 ]
 
-# Algorithmic FP64 operations (an FMA counts 2 flops, mul/add 1) of each op
-# for one helicity, from the arithmetic the operation must do, not from the
-# instructions the compiler emits.  Complex a*b = 6 flops, a*b+c = 8.
+# Algorithmic FP64 operations (an FMA counts 2 flops, mul/add 1) of each op,
+# from the arithmetic the operation must do, not from the instructions the
+# compiler emits.  Complex a*b = 6 flops, a*b+c = 8.  Each entry is
+# (flops shared by all top-helicity variants, flops per variant, variants):
+# one evaluation of the program covers the four (top, antitop) helicity
+# combinations of one gluon-helicity configuration.
+_SLASH = 16            # Jslash blocks: 8 complex adds
+_ROWJ = 56             # row spinor x Jslash: two 2x2 complex mat-vecs
+_QM = 40 + 16          # (qslash + m): two 2x2 mat-vecs with real/imaginary entries + mass terms
+_DEN = 24              # complex scaling by 1/den
 FLOPS = {
-    program.OP_EXT_G: 0,     # external states: counted separately (per event)
-    program.OP_EXT_UB: 0,
-    program.OP_EXT_V: 0,
-    # V3: 3 complex Minkowski dots (one complex x complex: 4*8-2 = 30, two
-    # real x complex: 2*(4*4-2) = 28), 3 complex scalings by 1/P^2 (6),
-    # 4 components of j*d + s2*J2 - s1*J1 (4*(2 + 8 + 8) = 72)
-    program.OP_V3: 30 + 28 + 6 + 72,
-    # V4: 3 complex dots (90), 3 structures x 4 components of a*X - b*Y
-    # (3*4*14 = 168), 3 x 4 complex scalings by 1/P^2 (24... as 3 scalars x2)
-    program.OP_V4: 90 + 168 + 18,
-    # FPRE/FSUF: Jslash blocks (8 complex adds = 16), two 2x2 complex
-    # mat-vecs (2*(4*6+2*2) = 56), (q+m) blocks: two 2x2 mat-vecs with
-    # real-or-imaginary entries (2*(4*4+2*2) = 40) plus mass terms (8*2 = 16),
-    # complex scale by 1/den (4*6 = 24)
-    program.OP_FPRE: 16 + 56 + 40 + 16 + 24,
-    program.OP_FSUF: 16 + 56 + 40 + 16 + 24,
-    program.OP_XROW: 16 + 56,
-    program.OP_YCOL: 16 + 56,
-    # bilinear: 8 complex products (48) + 12 complex adds (24)
-    program.OP_BIL: 48 + 24,
-    # amplitudes: 4 complex products + 3 complex adds
-    program.OP_AMP_SS: 4 * 6 + 3 * 2,
-    program.OP_AMP_VV: 4 * 6 + 3 * 2,
+    program.OP_EXT_G: (0, 0, 1),     # external states: per event, not counted
+    program.OP_EXT_UB: (0, 0, 2),
+    program.OP_EXT_V: (0, 0, 2),
+    # V3: 3 complex Minkowski dots (30 + 2*14), 3 complex scalings by 1/P^2
+    # (6), 4 components of j*d + s2*J2 - s1*J1 (4*(2 + 8 + 8))
+    program.OP_V3: (30 + 28 + 6 + 72, 0, 1),
+    # V4: 3 complex dots (90), 3 scalings (6), 3 x 4 components of a*X - b*Y (168)
+    program.OP_V4: (90 + 6 + 168, 0, 1),
+    program.OP_FPRE: (_SLASH, _ROWJ + _QM + _DEN, 2),
+    program.OP_FSUF: (_SLASH, _ROWJ + _QM + _DEN, 2),
+    program.OP_XROW: (_SLASH, _ROWJ, 2),
+    program.OP_YCOL: (_SLASH, _ROWJ, 2),
+    # bilinear: 8 complex products (48) + 12 complex adds (24), per variant
+    program.OP_BIL: (0, 48 + 24, 4),
+    # amplitudes: 4 complex products + 3 complex adds, per variant
+    program.OP_AMP_SS: (0, 4 * 6 + 3 * 2, 4),
+    program.OP_AMP_VV: (0, 4 * 6 + 3 * 2, 4),
 }
 JAMP_UPDATE_FLOPS = 2
 
 
 def algorithmic_flops(prog: program.Program) -> dict:
-    """FP64 flops per helicity: diagrams (ops + jamp updates) and colour sum
-    (symmetric quadratic form over A and B: 2 * nc^2 multiply-adds)."""
-    diag = sum(FLOPS[op[0]] for op in prog.ops) + JAMP_UPDATE_FLOPS * len(prog.scatter)
+    """FP64 flops per good helicity (all four top combinations good): the
+    diagram program (ops + jamp updates) shared over four helicities, and the
+    colour sum (symmetric quadratic form over A and B)."""
+    unit = 0
+    for op in prog.ops:
+        sh, pv, nv = FLOPS[op[0]]
+        unit += sh + pv * nv
+    unit += JAMP_UPDATE_FLOPS * 4 * len(prog.scatter)
     nc = prog.ncolor
     csum = 2 * (nc * (nc + 1) // 2) * 2 + 2 * nc
-    return dict(diagram=diag, colour=csum)
+    return dict(diagram=unit / 4.0, colour=csum)
 
 
 def _arr(name, vals, per_line=16):
@@ -76,8 +82,8 @@ def _arr(name, vals, per_line=16):
 
 def emit(path: str, max_gluons: int = 6, list_path: str | None = None) -> None:
     """Write the table include file ``path`` and, next to it (or at
-    ``list_path``), mg_proc_list.h with one X(index, ngluon, nslot, ncolor)
-    entry per process for the kernel instantiations."""
+    ``list_path``), mg_proc_list.h with one X(index, ngluon, nslot_gluon,
+    nslot_top, ncolor) entry per process for the kernel instantiations."""
     lines = ["/* generated by paper_2510_05392_gb300.compiler.emit -- do not edit */",
              "#pragma once", "#include <stdint.h>", ""]
     rows = []
@@ -98,9 +104,10 @@ def emit(path: str, max_gluons: int = 6, list_path: str | None = None) -> None:
         iden = 256 * math.factorial(n - 2)
         rows.append(
             f'  {{"{name}", "{proc}", {n}, {n + 2}, {prog.ndiagrams}, {prog.nterms}, '
-            f'{prog.ncolor}, {prog.nslot}, {len(prog.ops)}, {len(prog.scatter)}, {D}LL, '
-            f'{iden}.0, {fl["diagram"]}.0, {fl["colour"]}.0, OPS_{name}, SCAT_{name}, CHAT_{name}}},')
-        xlist.append(f"X({len(rows) - 1}, {n}, {prog.nslot}, {prog.ncolor})")
+            f'{prog.ncolor}, {prog.nslot}, {prog.nslot_f}, {len(prog.ops)}, {len(prog.scatter)}, '
+            f'{D}LL, {iden}.0, {fl["diagram"]!r}, {fl["colour"]}.0, OPS_{name}, SCAT_{name}, '
+            f'CHAT_{name}}},')
+        xlist.append(f"X({len(rows) - 1}, {n}, {prog.nslot}, {prog.nslot_f}, {prog.ncolor})")
         lines.append("")
     lines.append("static const mg_proc_table MG_PROC_TABLES[] = {")
     lines.extend(rows)

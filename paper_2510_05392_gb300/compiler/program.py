@@ -56,7 +56,8 @@ class Program:
     ncolor: int
     ops: list = field(default_factory=list)        # list of 8-int records
     scatter: list = field(default_factory=list)    # jamp*4 + coef
-    nslot: int = 0
+    nslot: int = 0                                 # gluon-wavefunction slots (1 variant)
+    nslot_f: int = 0                               # top-line slots (2 variants)
     ndiagrams: int = 0
     nterms: int = 0
     perms: list = field(default_factory=list)      # colour-flow orderings
@@ -258,36 +259,53 @@ def build_program(n: int, order: str = "middle") -> Program:
         B._emit(code, [], ins, [off, len(scatter) - off])
 
     # ------------------------------------------------ slot allocation ----
+    # Three pools, by how many top-helicity variants an object carries:
+    #   G: gluon wavefunctions (EXT_G, V3, V4)             1 variant
+    #   F: top-line objects (ubar/v side, FPRE, FSUF, XROW, YCOL)  2 variants
+    #      (the helicity of the top for ubar-side objects, of the antitop
+    #      for v-side ones)
+    #   the bilinear G0 = ubar gamma v                   4 variants, own storage
+    pool_of = {}
+    for code, outs, ins, extra in B.ops:
+        for o in outs:
+            if code in (OP_EXT_G, OP_V3, OP_V4):
+                pool_of[o] = "G"
+            elif code == OP_BIL:
+                pool_of[o] = "B"
+            else:
+                pool_of[o] = "F"
     last_use = {}
     for i, (code, outs, ins, extra) in enumerate(B.ops):
         for o in ins:
             last_use[o] = i
     slot_of = {}
-    free = []
-    nslot = 0
+    free = {"G": [], "F": [], "B": []}
+    nslot = {"G": 0, "F": 0, "B": 0}
     records = []
     for i, (code, outs, ins, extra) in enumerate(B.ops):
         in_slots = [slot_of[o] for o in ins]
         out_slots = []
         for o in outs:
+            pl = pool_of[o]
             if o not in last_use:
-                out_slots.append(-1)  # never used (should not happen)
-                continue
-            if free:
-                free.sort(reverse=True)
-                s = free.pop()
+                raise AssertionError("unused wavefunction")
+            if free[pl]:
+                free[pl].sort(reverse=True)
+                s_ = free[pl].pop()
             else:
-                s = nslot
-                nslot += 1
-            slot_of[o] = s
-            out_slots.append(s)
+                s_ = nslot[pl]
+                nslot[pl] += 1
+            slot_of[o] = s_
+            out_slots.append(s_)
         # release inputs whose last use is this op (outputs never alias inputs)
         for o in set(ins):
             if last_use.get(o) == i:
-                free.append(slot_of[o])
+                free[pool_of[o]].append(slot_of[o])
         records.append(_record(code, out_slots, in_slots, extra))
+    assert nslot["B"] <= 1
     prog = Program(n=n, npar=n + 2, ncolor=len(perms), ops=records, scatter=scatter,
-                   nslot=nslot, ndiagrams=P.ndiagrams, nterms=len(P.diagrams), perms=perms)
+                   nslot=nslot["G"], nslot_f=nslot["F"], ndiagrams=P.ndiagrams,
+                   nterms=len(P.diagrams), perms=perms)
     return prog
 
 

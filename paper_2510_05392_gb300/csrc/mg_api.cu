@@ -21,7 +21,8 @@ struct mg_process {
     int32_t *d_ops;
     int32_t *d_scat;
     double *d_cup;
-    int *d_hel;          // good-helicity list (device)
+    int *d_units;        // work units (device): gluon config << 4 | top-helicity mask
+    int nunits;
     int ngood;           // -1 until filtered
     uint8_t mask[256];
     int tpe, block;      // launch shape
@@ -94,32 +95,51 @@ void free_proc(mg_process *p) {
     cudaFree(p->d_ops);
     cudaFree(p->d_scat);
     cudaFree(p->d_cup);
-    cudaFree(p->d_hel);
+    cudaFree(p->d_units);
     free(p);
 }
 
+// Good-helicity mask -> work units: one per gluon-helicity configuration g
+// that has a good helicity, with the 4-bit mask of its good (top, antitop)
+// combinations (bit 2*bt + btb).
 int set_hel_list(mg_process *p, const uint8_t *mask) {
-    const int nhel = 1 << p->tab->npar;
-    int list[256];
-    int ng = 0;
-    for (int h = 0; h < nhel; h++) {
-        p->mask[h] = mask[h] ? 1 : 0;
-        if (mask[h]) list[ng++] = h;
+    const int npar = p->tab->npar, ng = p->tab->ngluon;
+    int units[64];
+    int nu = 0, ngood = 0;
+    for (int h = 0; h < (1 << npar); h++) p->mask[h] = mask[h] ? 1 : 0;
+    for (int g = 0; g < (1 << ng); g++) {
+        int m = 0;
+        for (int v = 0; v < 4; v++) {
+            int h = ((v >> 1) << (npar - 1 - 2)) | ((v & 1) << (npar - 1 - 3));
+            for (int j = 0; j < ng; j++) {
+                const int ip = (j < 2) ? j : j + 2;
+                h |= ((g >> j) & 1) << (npar - 1 - ip);
+            }
+            if (mask[h]) {
+                m |= 1 << v;
+                ngood++;
+            }
+        }
+        if (m) units[nu++] = (g << 4) | m;
     }
-    if (ng > 0) MG_CUDA(cudaMemcpy(p->d_hel, list, sizeof(int) * ng, cudaMemcpyHostToDevice));
-    p->ngood = ng;
+    if (nu > 0) MG_CUDA(cudaMemcpy(p->d_units, units, sizeof(int) * nu, cudaMemcpyHostToDevice));
+    p->nunits = nu;
+    p->ngood = ngood;
     return MG_OK;
 }
 
 int default_tpe(int npar) {
-    // threads per event: enough helicity slots per event for small
-    // processes, one thread per event for the large ones
+    // threads per event (each thread takes 2^ngluon / tpe work units of
+    // four helicities): enough threads for small batches of the small
+    // processes, few redundant per-event kinematics for the large ones
+    // (measured on GB300: ggtt best at 2, ggttgg flat from 1 to 8, ggttggg
+    // best at 8, ggttgggg needs many threads per event for small batches)
     switch (npar) {
-        case 4: return 16;
-        case 5: return 8;
+        case 4: return 2;
+        case 5: return 2;
         case 6: return 4;
-        case 7: return 2;
-        default: return 1;
+        case 7: return 8;
+        default: return 16;
     }
 }
 
@@ -199,7 +219,7 @@ int mg_process_create(const char *process, const mg_params *params, mg_process *
     TRY(cudaMalloc(&p->d_ops, sizeof(int32_t) * 8 * t->nops));
     TRY(cudaMalloc(&p->d_scat, sizeof(int32_t) * (t->nscat > 0 ? t->nscat : 1)));
     TRY(cudaMalloc(&p->d_cup, sizeof(double) * ntri));
-    TRY(cudaMalloc(&p->d_hel, sizeof(int) * 256));
+    TRY(cudaMalloc(&p->d_units, sizeof(int) * 64));
     TRY(cudaMemcpy(p->d_ops, t->ops, sizeof(int32_t) * 8 * t->nops, cudaMemcpyHostToDevice));
     if (t->nscat > 0)
         TRY(cudaMemcpy(p->d_scat, t->scat, sizeof(int32_t) * t->nscat, cudaMemcpyHostToDevice));
@@ -236,6 +256,7 @@ int mg_process_info(const mg_process *p, mg_info *o) {
     o->nhel = 1 << t->npar;
     o->ngood = p->ngood;
     o->nslot = t->nslot;
+    o->nslot_top = t->nslot_top;
     o->nops = t->nops;
     o->njamp_updates = t->nscat;
     o->denom = t->denom;
@@ -296,7 +317,7 @@ int mg_filter_helicities(mg_process *p, const double *mom, int64_t n, void *stre
     e = cudaMalloc(&dmask, nhel);
     if (e == cudaSuccess) e = cudaMemsetAsync(mh, 0, sizeof(double) * n * nhel, s);
     if (e == cudaSuccess)
-        e = mg_launch_sigmakin(dev_view(p), mom, n, p->d_hel, nhel, 32, p->block, nullptr, mh, s);
+        e = mg_launch_sigmakin(dev_view(p), mom, n, p->d_units, p->nunits, 32, p->block, nullptr, mh, s);
     if (e == cudaSuccess) e = mg_launch_helmask(mh, n, nhel, 1e-14, dmask, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(mask, dmask, nhel, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -331,8 +352,8 @@ static int sigmakin_impl(mg_process *p, const double *mom, int64_t nevt, double 
         return MG_OK;
     }
     int tpe = p->tpe;
-    while (tpe > 1 && tpe > p->ngood) tpe >>= 1;
-    MG_CUDA(mg_launch_sigmakin(dev_view(p), mom, nevt, p->d_hel, p->ngood, tpe, p->block, me,
+    while (tpe > 1 && tpe > p->nunits) tpe >>= 1;
+    MG_CUDA(mg_launch_sigmakin(dev_view(p), mom, nevt, p->d_units, p->nunits, tpe, p->block, me,
                                me_hel, s));
     return MG_OK;
 }
@@ -411,7 +432,7 @@ extern "C" int mg_filter_helicities_noalloc(mg_process *p, const double *mom, in
     cudaError_t e = cudaMemsetAsync(mh, 0, sizeof(double) * n * nhel, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(dmask, 0, nhel, s);
     if (e == cudaSuccess)
-        e = mg_launch_sigmakin(dev_view(p), mom, n, p->d_hel, nhel, 32, p->block, nullptr, mh, s);
+        e = mg_launch_sigmakin(dev_view(p), mom, n, p->d_units, p->nunits, 32, p->block, nullptr, mh, s);
     if (e == cudaSuccess) e = mg_launch_helmask(mh, n, nhel, 1e-14, dmask, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(mask, dmask, nhel, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

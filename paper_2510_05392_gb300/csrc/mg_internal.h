@@ -13,7 +13,10 @@ extern "C" {
 typedef struct {
     const char *name;        // "ggttgg"
     const char *process;     // "g g > t t~ g g"
-    int ngluon, npar, ndiagrams, nterms, ncolor, nslot, nops, nscat;
+    int ngluon, npar, ndiagrams, nterms, ncolor;
+    int nslot;               // gluon-wavefunction slots (one variant)
+    int nslot_top;           // top-line slots (two helicity variants)
+    int nops, nscat;
     long long denom;         // colour-matrix common denominator D
     double iden;             // averaging factor
     double flops_diagram;    // algorithmic FP64 flops per helicity (diagrams)
@@ -60,8 +63,10 @@ typedef struct {
 #ifdef __cplusplus
 #include <cuda_runtime.h>
 // Launchers (mg_kernels.cu).  All asynchronous on `stream`.
+// units: work units (gluon-helicity configuration << 4 | mask of the good
+// (top, antitop) helicity combinations, bit 2*bt + btb), nunits of them.
 cudaError_t mg_launch_sigmakin(const mg_dev_proc &dp, const double *mom, int64_t nevt,
-                               const int *hel_list, int ngood, int tpe, int block, double *me,
+                               const int *units, int nunits, int tpe, int block, double *me,
                                double *me_hel, cudaStream_t stream);
 cudaError_t mg_launch_helmask(const double *me_hel, int64_t n, int nhel, double rel,
                               unsigned char *mask, cudaStream_t stream);

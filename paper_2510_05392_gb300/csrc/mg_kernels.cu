@@ -1,7 +1,8 @@
-// Diagram kernel: one thread per (event, helicity slot) executes the
-// process's wavefunction/amplitude program (compiler/program.py) and the
-// FP64 colour sum, then the helicity slots of an event are reduced with warp
-// shuffles.
+// Diagram kernel: `tpe` threads per event share its work units (one
+// gluon-helicity configuration with the four top/antitop helicities each),
+// execute the process's wavefunction/amplitude program
+// (compiler/program.py) and the FP64 colour sum, and the event's threads are
+// reduced with warp shuffles.
 //
 // Structure of the paper's sigmaKin (Sec. 2.2): per event and good helicity,
 // external wavefunctions -> internal wavefunctions -> amplitudes -> jamps ->
@@ -14,7 +15,9 @@
 // (warp-broadcast) load, the dispatch is warp-uniform, and wavefunctions,
 // jamps and per-event kinematics live in per-thread local memory.  Per-event
 // quantities (momentum sums, 1/P^2, top propagators) are computed once per
-// thread and reused by all of its helicities.
+// thread and reused by all of its helicities; gluon wavefunctions are shared
+// by the four top/antitop helicities of a unit (helicity recycling of the
+// FP64 work that does not depend on the top helicities).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -82,79 +85,118 @@ __device__ void kinematics(Kin<NG> &k, const double *__restrict__ p, double mt, 
     }
 }
 
-__device__ __forceinline__ int hel_sign(int hel, int npar, int ip) {
-    return ((hel >> (npar - 1 - ip)) & 1) ? 1 : -1;
+// Full helicity index of gluon configuration g (bit j = helicity of gluon j,
+// gluons in particle order) and top/antitop helicity bits bt, btb.
+template <int NG>
+__device__ __forceinline__ int helicity_index(int g, int bt, int btb) {
+    constexpr int NPAR = NG + 2;
+    int h = (bt << (NPAR - 1 - 2)) | (btb << (NPAR - 1 - 3));
+#pragma unroll
+    for (int j = 0; j < NG; j++) {
+        const int ip = (j < 2) ? j : j + 2;
+        h |= ((g >> j) & 1) << (NPAR - 1 - ip);
+    }
+    return h;
 }
 
-// Executes the program for one helicity; returns sum_ij D*C_ij Re(J_i^* J_j).
-template <int NG, int NSLOT, int NC>
-__device__ double run_program(const Kin<NG> &k, int hel, const int4 *__restrict__ ops, int nops,
-                              const int *__restrict__ scat, const double *__restrict__ cup,
-                              double mt, cx (*W)[4], cx *J) {
-    constexpr int NPAR = NG + 2;
-    for (int c = 0; c < NC; c++) J[c] = mk(0.0, 0.0);
+// One evaluation of the program: gluon-helicity configuration g and all four
+// (top, antitop) helicity combinations v = 2*bt + btb at once.  Gluon
+// wavefunctions (pool WG) are computed once for the four; top-line objects
+// (pool WF) carry the two helicities of the top (ubar side) or of the antitop
+// (v side); the bilinear G0, the amplitudes and the jamps carry all four.
+// Writes me4[v] = sum_ij D*C_ij Re(J_v,i^* J_v,j).
+template <int NG, int NSG, int NSF, int NC>
+__device__ void run_unit(const Kin<NG> &k, int g, const int4 *__restrict__ ops, int nops,
+                         const int *__restrict__ scat, const double *__restrict__ cup, double mt,
+                         cx (*WG)[4], cx (*WF)[2][4], cx (*G0)[4], cx (*J)[NC], double *me4) {
+    for (int v = 0; v < 4; v++)
+        for (int c = 0; c < NC; c++) J[v][c] = mk(0.0, 0.0);
     for (int i = 0; i < nops; i++) {
         const int4 a = __ldg(ops + 2 * i);
         const int4 b = __ldg(ops + 2 * i + 1);
         switch (a.x) {
-            case MG_OP_EXT_G:
-                ext_gluon(k.P[a.z], hel_sign(hel, NPAR, a.z), a.w != 0, W[a.y]);
+            case MG_OP_EXT_G: {
+                const int gi = (a.z < 2) ? a.z : a.z - 2;
+                ext_gluon(k.P[a.z], ((g >> gi) & 1) ? 1 : -1, a.w != 0, WG[a.y]);
                 break;
+            }
             case MG_OP_EXT_UB:
-                ext_ubar(k.P[2], hel_sign(hel, NPAR, 2), W[a.y]);
+                ext_ubar(k.P[2], -1, WF[a.y][0]);
+                ext_ubar(k.P[2], 1, WF[a.y][1]);
                 break;
             case MG_OP_EXT_V:
-                ext_v(k.P[3], hel_sign(hel, NPAR, 3), W[a.y]);
+                ext_v(k.P[3], -1, WF[a.y][0]);
+                ext_v(k.P[3], 1, WF[a.y][1]);
                 break;
             case MG_OP_V3:
-                vvv_current(W[a.z], k.K[b.x], W[a.w], k.K[b.y], k.IP2[b.x | b.y], W[a.y]);
+                vvv_current(WG[a.z], k.K[b.x], WG[a.w], k.K[b.y], k.IP2[b.x | b.y], WG[a.y]);
                 break;
             case MG_OP_V4:
-                vvvv_currents(W[b.x], W[b.y], W[b.z], k.IP2[b.w], W[a.y], W[a.z], W[a.w]);
+                vvvv_currents(WG[b.x], WG[b.y], WG[b.z], k.IP2[b.w], WG[a.y], WG[a.z], WG[a.w]);
                 break;
             case MG_OP_FPRE: {
-                const Slash s = slash_blocks(W[a.w]);
-                cx t[4], o[4];
-                row_slash(W[a.z], s, t);
-                row_qm(t, k.QP[b.x], mt, o);
+                const Slash s = slash_blocks(WG[a.w]);
                 const cx d = k.DP[b.x];
-                for (int m = 0; m < 4; m++) W[a.y][m] = o[m] * d;
+                for (int v = 0; v < 2; v++) {
+                    cx t[4], o[4];
+                    row_slash(WF[a.z][v], s, t);
+                    row_qm(t, k.QP[b.x], mt, o);
+                    for (int m = 0; m < 4; m++) WF[a.y][v][m] = o[m] * d;
+                }
                 break;
             }
             case MG_OP_FSUF: {
-                const Slash s = slash_blocks(W[a.w]);
-                cx t[4], o[4];
-                slash_col(s, W[a.z], t);
-                qm_col(k.QS[b.x], mt, t, o);
+                const Slash s = slash_blocks(WG[a.w]);
                 const cx d = k.DS[b.x];
-                for (int m = 0; m < 4; m++) W[a.y][m] = o[m] * d;
+                for (int v = 0; v < 2; v++) {
+                    cx t[4], o[4];
+                    slash_col(s, WF[a.z][v], t);
+                    qm_col(k.QS[b.x], mt, t, o);
+                    for (int m = 0; m < 4; m++) WF[a.y][v][m] = o[m] * d;
+                }
                 break;
             }
             case MG_OP_XROW: {
-                const Slash s = slash_blocks(W[a.w]);
-                row_slash(W[a.z], s, W[a.y]);
+                const Slash s = slash_blocks(WG[a.w]);
+                for (int v = 0; v < 2; v++) row_slash(WF[a.z][v], s, WF[a.y][v]);
                 break;
             }
             case MG_OP_YCOL: {
-                const Slash s = slash_blocks(W[a.z]);
-                slash_col(s, W[a.w], W[a.y]);
+                const Slash s = slash_blocks(WG[a.z]);
+                for (int v = 0; v < 2; v++) slash_col(s, WF[a.w][v], WF[a.y][v]);
                 break;
             }
             case MG_OP_BIL:
-                bilinear(W[a.z], W[a.w], W[a.y]);
+                for (int bt = 0; bt < 2; bt++)
+                    for (int btb = 0; btb < 2; btb++) bilinear(WF[a.z][bt], WF[a.w][btb], G0[2 * bt + btb]);
                 break;
             case MG_OP_AMP_SS:
             case MG_OP_AMP_VV: {
-                const cx amp = (a.x == MG_OP_AMP_SS) ? sdot(W[a.z], W[a.w]) : mdot(W[a.z], W[a.w]);
+                cx amp[4];
+                if (a.x == MG_OP_AMP_SS) {
+                    for (int bt = 0; bt < 2; bt++)
+                        for (int btb = 0; btb < 2; btb++)
+                            amp[2 * bt + btb] = sdot(WF[a.z][bt], WF[a.w][btb]);
+                } else {
+                    for (int v = 0; v < 4; v++) amp[v] = mdot(G0[v], WG[a.w]);
+                }
                 const int end = b.x + b.y;
                 for (int s = b.x; s < end; s++) {
                     const int e = __ldg(scat + s);
                     const int j = e >> 2;
                     switch (e & 3) {
-                        case 0: J[j] = J[j] + amp; break;
-                        case 1: J[j] = J[j] - amp; break;
-                        case 2: J[j] = J[j] + mk(-amp.i, amp.r); break;
-                        default: J[j] = J[j] + mk(amp.i, -amp.r); break;
+                        case 0:
+                            for (int v = 0; v < 4; v++) J[v][j] = J[v][j] + amp[v];
+                            break;
+                        case 1:
+                            for (int v = 0; v < 4; v++) J[v][j] = J[v][j] - amp[v];
+                            break;
+                        case 2:
+                            for (int v = 0; v < 4; v++) J[v][j] = J[v][j] + mk(-amp[v].i, amp[v].r);
+                            break;
+                        default:
+                            for (int v = 0; v < 4; v++) J[v][j] = J[v][j] + mk(amp[v].i, -amp[v].r);
+                            break;
                     }
                 }
                 break;
@@ -163,27 +205,31 @@ __device__ double run_program(const Kin<NG> &k, int hel, const int4 *__restrict_
                 break;
         }
     }
-    // colour sum over the packed upper triangle (diagonal D*C_ii,
-    // off-diagonal 2*D*C_ij): sum_i A_i z_i + B_i y_i
-    double me = 0.0;
+    // colour sum over the packed upper triangle (diagonal D*C_ii, off-diagonal
+    // 2*D*C_ij), the four helicity combinations sharing each matrix entry
+    double me[4] = {0.0, 0.0, 0.0, 0.0};
     const double *c = cup;
     for (int i = 0; i < NC; i++) {
-        double zr = 0.0, zi = 0.0;
+        double zr[4] = {0.0, 0.0, 0.0, 0.0}, zi[4] = {0.0, 0.0, 0.0, 0.0};
         for (int j = i; j < NC; j++) {
             const double cij = __ldg(c++);
-            zr = fma(cij, J[j].r, zr);
-            zi = fma(cij, J[j].i, zi);
+#pragma unroll
+            for (int v = 0; v < 4; v++) {
+                zr[v] = fma(cij, J[v][j].r, zr[v]);
+                zi[v] = fma(cij, J[v][j].i, zi[v]);
+            }
         }
-        me = fma(J[i].r, zr, fma(J[i].i, zi, me));
+#pragma unroll
+        for (int v = 0; v < 4; v++) me[v] = fma(J[v][i].r, zr[v], fma(J[v][i].i, zi[v], me[v]));
     }
-    return me;
+    for (int v = 0; v < 4; v++) me4[v] = me[v];
 }
 
-template <int NG, int NSLOT, int NC>
+template <int NG, int NSG, int NSF, int NC>
 __global__ void __launch_bounds__(256)
     k_sigmakin(const double *__restrict__ mom, long long nevt, const int4 *__restrict__ ops,
                int nops, const int *__restrict__ scat, const double *__restrict__ cup,
-               const int *__restrict__ hel, int ngood, int tpe, double mt, double wt,
+               const int *__restrict__ units, int nunits, int tpe, double mt, double wt,
                double factor, double *__restrict__ me, double *__restrict__ me_hel) {
     constexpr int NPAR = NG + 2;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -193,13 +239,20 @@ __global__ void __launch_bounds__(256)
     if (e < nevt) {
         Kin<NG> k;
         kinematics<NG>(k, mom + e * (NPAR * 4), mt, wt);
-        cx W[NSLOT][4];
-        cx J[NC];
-        for (int ih = s; ih < ngood; ih += tpe) {
-            const int h = __ldg(hel + ih);
-            const double mh = run_program<NG, NSLOT, NC>(k, h, ops, nops, scat, cup, mt, W, J);
-            if (me_hel) me_hel[e * (1LL << NPAR) + h] = mh * factor;
-            sum += mh;
+        cx WG[NSG > 0 ? NSG : 1][4];
+        cx WF[NSF > 0 ? NSF : 1][2][4];
+        cx G0[4][4];
+        cx J[4][NC];
+        for (int iu = s; iu < nunits; iu += tpe) {
+            const int u = __ldg(units + iu);
+            const int g = u >> 4, mask = u & 15;
+            double me4[4];
+            run_unit<NG, NSG, NSF, NC>(k, g, ops, nops, scat, cup, mt, WG, WF, G0, J, me4);
+            for (int v = 0; v < 4; v++) {
+                if (!((mask >> v) & 1)) continue;
+                sum += me4[v];
+                if (me_hel) me_hel[e * (1LL << NPAR) + helicity_index<NG>(g, v >> 1, v & 1)] = me4[v] * factor;
+            }
         }
     }
     for (int o = tpe >> 1; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
@@ -224,18 +277,18 @@ __global__ void k_helmask(const double *__restrict__ mh, long long n, int nhel, 
 }  // namespace
 
 cudaError_t mg_launch_sigmakin(const mg_dev_proc &dp, const double *mom, int64_t nevt,
-                               const int *hel_list, int ngood, int tpe, int block, double *me,
+                               const int *units, int nunits, int tpe, int block, double *me,
                                double *me_hel, cudaStream_t stream) {
     if (nevt <= 0) return cudaSuccess;
     const long long threads = (long long)nevt * tpe;
     const long long grid = (threads + block - 1) / block;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
     switch (dp.table_index) {
-#define MG_LAUNCH(IDX, NG, NSLOT, NC)                                                            \
+#define MG_LAUNCH(IDX, NG, NSG, NSF, NC)                                                         \
     case IDX:                                                                                    \
-        k_sigmakin<NG, NSLOT, NC><<<(unsigned)grid, block, 0, stream>>>(                         \
-            mom, nevt, reinterpret_cast<const int4 *>(dp.ops), dp.nops, dp.scat, dp.cup, hel_list, \
-            ngood, tpe, dp.mt, dp.wt, dp.factor, me, me_hel);                                    \
+        k_sigmakin<NG, NSG, NSF, NC><<<(unsigned)grid, block, 0, stream>>>(                      \
+            mom, nevt, reinterpret_cast<const int4 *>(dp.ops), dp.nops, dp.scat, dp.cup, units,   \
+            nunits, tpe, dp.mt, dp.wt, dp.factor, me, me_hel);                                   \
         break;
         MG_PROC_LIST(MG_LAUNCH)
 #undef MG_LAUNCH

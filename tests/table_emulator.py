@@ -88,49 +88,49 @@ def run(n, mom, mt=173.0, wt=1.4915, alphas=0.118, per_helicity=False):
     mh_all = np.zeros((nev, 1 << npar))
     for h in range(1 << npar):
         sg = lambda ip: 1 if (h >> (npar - 1 - ip)) & 1 else -1
-        W = {}
+        WG, WF, WB = {}, {}, {}   # slot pools: gluon, top-line, bilinear
         J = np.zeros((nev, prog.ncolor), complex)
         for r in prog.ops:
             c = r[0]
             if c == P.OP_EXT_G:
-                W[r[1]] = _pol(mom[:, r[2]], sg(r[2]), r[3] == 1)
+                WG[r[1]] = _pol(mom[:, r[2]], sg(r[2]), r[3] == 1)
             elif c == P.OP_EXT_UB:
-                W[r[1]] = _ubar(p3, sg(2))
+                WF[r[1]] = _ubar(p3, sg(2))
             elif c == P.OP_EXT_V:
-                W[r[1]] = _v(p4, sg(3))
+                WF[r[1]] = _v(p4, sg(3))
             elif c == P.OP_V3:
-                J1, J2, K1, K2 = W[r[2]], W[r[3]], K(r[4]), K(r[5])
+                J1, J2, K1, K2 = WG[r[2]], WG[r[3]], K(r[4]), K(r[5])
                 P_ = K1 + K2
                 out = (_mdot(J1, J2)[:, None] * (K1 - K2) + J2 * _mdot(K1 + 2 * K2, J1)[:, None]
                        - J1 * _mdot(2 * K1 + K2, J2)[:, None])
-                W[r[1]] = out / _mdot(P_, P_)[:, None]
+                WG[r[1]] = out / _mdot(P_, P_)[:, None]
             elif c == P.OP_V4:
-                X, Y, Z = W[r[4]], W[r[5]], W[r[6]]
+                X, Y, Z = WG[r[4]], WG[r[5]], WG[r[6]]
                 Kt = K(r[7])
                 inv = 1 / _mdot(Kt, Kt)[:, None]
                 xy, xz, yz = _mdot(X, Y)[:, None], _mdot(X, Z)[:, None], _mdot(Y, Z)[:, None]
-                W[r[1]] = (xz * Y - yz * X) * inv
-                W[r[2]] = (xy * Z - yz * X) * inv
-                W[r[3]] = (xy * Z - xz * Y) * inv
+                WG[r[1]] = (xz * Y - yz * X) * inv
+                WG[r[2]] = (xy * Z - yz * X) * inv
+                WG[r[3]] = (xy * Z - xz * Y) * inv
             elif c in (P.OP_FPRE, P.OP_FSUF):
                 Ks = K(r[4])
                 q = (p3 - Ks) if c == P.OP_FPRE else (Ks - p4)
                 den = 1 / (_mdot(q, q) - mt * mt + 1j * mt * wt)
                 qm = _slash(q.astype(complex)) + mt * np.eye(4)
                 if c == P.OP_FPRE:
-                    t = np.einsum("ei,eij->ej", W[r[2]], _slash(W[r[3]]))
-                    W[r[1]] = np.einsum("ei,eij->ej", t, qm) * den[:, None]
+                    t = np.einsum("ei,eij->ej", WF[r[2]], _slash(WG[r[3]]))
+                    WF[r[1]] = np.einsum("ei,eij->ej", t, qm) * den[:, None]
                 else:
-                    t = np.einsum("eij,ej->ei", _slash(W[r[3]]), W[r[2]])
-                    W[r[1]] = np.einsum("eij,ej->ei", qm, t) * den[:, None]
+                    t = np.einsum("eij,ej->ei", _slash(WG[r[3]]), WF[r[2]])
+                    WF[r[1]] = np.einsum("eij,ej->ei", qm, t) * den[:, None]
             elif c == P.OP_XROW:
-                W[r[1]] = np.einsum("ei,eij->ej", W[r[2]], _slash(W[r[3]]))
+                WF[r[1]] = np.einsum("ei,eij->ej", WF[r[2]], _slash(WG[r[3]]))
             elif c == P.OP_YCOL:
-                W[r[1]] = np.einsum("eij,ej->ei", _slash(W[r[2]]), W[r[3]])
+                WF[r[1]] = np.einsum("eij,ej->ei", _slash(WG[r[2]]), WF[r[3]])
             elif c == P.OP_BIL:
-                W[r[1]] = np.einsum("ei,mij,ej->em", W[r[2]], _G, W[r[3]])
+                WB[r[1]] = np.einsum("ei,mij,ej->em", WF[r[2]], _G, WF[r[3]])
             elif c in (P.OP_AMP_SS, P.OP_AMP_VV):
-                a = (W[r[2]] * W[r[3]]).sum(-1) if c == P.OP_AMP_SS else _mdot(W[r[2]], W[r[3]])
+                a = (WF[r[2]] * WF[r[3]]).sum(-1) if c == P.OP_AMP_SS else _mdot(WB[r[2]], WG[r[3]])
                 for e in prog.scatter[r[4]:r[4] + r[5]]:
                     J[:, e >> 2] += a * [1, -1, 1j, -1j][e & 3]
         mh = np.einsum("ei,ij,ej->e", J.conj(), C, J).real

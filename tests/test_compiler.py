@@ -41,22 +41,34 @@ def test_colour_matrix_bit_exact_vs_oracle(n):
     assert [tuple(x) for x in a[2]] == [tuple(x) for x in b[2]]
 
 
+# pool of every operand: G gluon wavefunctions, F top-line objects, B bilinear
+_POOLS = {  # opcode: (output pools, [(field, pool) of inputs])
+    program.OP_EXT_G: ("G", []), program.OP_EXT_UB: ("F", []), program.OP_EXT_V: ("F", []),
+    program.OP_V3: ("G", [(2, "G"), (3, "G")]),
+    program.OP_V4: ("GGG", [(4, "G"), (5, "G"), (6, "G")]),
+    program.OP_FPRE: ("F", [(2, "F"), (3, "G")]), program.OP_FSUF: ("F", [(2, "F"), (3, "G")]),
+    program.OP_XROW: ("F", [(2, "F"), (3, "G")]), program.OP_YCOL: ("F", [(2, "G"), (3, "F")]),
+    program.OP_BIL: ("B", [(2, "F"), (3, "F")]),
+    program.OP_AMP_SS: ("", [(2, "F"), (3, "F")]), program.OP_AMP_VV: ("", [(2, "B"), (3, "G")]),
+}
+
+
 @pytest.mark.parametrize("n", [2, 3, 4, 5])
 def test_program_slots_well_formed(n):
+    """Every operand is read after it is written, in its own pool, and no
+    output overwrites an input of the same operation."""
     prog = program.build_program(n)
+    size = {"G": prog.nslot, "F": prog.nslot_f, "B": 1}
     written = set()
     for r in prog.ops:
-        c = r[0]
-        ins = {program.OP_V3: r[2:4], program.OP_V4: r[4:7], program.OP_FPRE: r[2:4],
-               program.OP_FSUF: r[2:4], program.OP_XROW: r[2:4], program.OP_YCOL: r[2:4],
-               program.OP_BIL: r[2:4], program.OP_AMP_SS: r[2:4],
-               program.OP_AMP_VV: r[2:4]}.get(c, [])
-        outs = {program.OP_V4: r[1:4]}.get(c, [r[1]] if c not in (program.OP_AMP_SS, program.OP_AMP_VV) else [])
-        for s in ins:
-            assert s in written
-        for s in outs:
-            assert 0 <= s < prog.nslot
-            assert s not in ins
+        outp, ins = _POOLS[r[0]]
+        in_keys = [(pl, r[f]) for f, pl in ins]
+        for key in in_keys:
+            assert key in written, (r, key)
+        outs = [(pl, r[1 + i]) for i, pl in enumerate(outp)]
+        for pl, s in outs:
+            assert 0 <= s < size[pl]
+            assert (pl, s) not in in_keys
         written.update(outs)
     assert all(0 <= (e >> 2) < prog.ncolor for e in prog.scatter)
 

@@ -63,7 +63,10 @@ typedef struct {
     double alphas;   /* fixed strong coupling, g_s = sqrt(4 pi alphas)      */
     int hel_mode;    /* MG_HEL_FILTERED (filter first) or MG_HEL_ALL        */
     int precision;   /* MG_FP64 (all FP64) or MG_MIXED_BF16 (FP64 diagrams, */
-                     /* tensor-core colour sum)                             */
+                     /* colour sum on tcgen05 tensor cores: jamps split in  */
+                     /* three BF16 pieces, D*C in two, FP32 accumulation,   */
+                     /* FP64 epilogue; processes with <= 128 colour flows;  */
+                     /* mg_sigmakin_hel is then MG_ERR_UNSUPPORTED)        */
 } mg_params;
 
 typedef struct {
@@ -126,6 +129,13 @@ int mg_sigmakin(mg_process *p, const double *momenta_dev, int64_t nevt, double *
  * are not good are written as 0.  me_out_dev may be NULL. */
 int mg_sigmakin_hel(mg_process *p, const double *momenta_dev, int64_t nevt, double *me_out_dev,
                     double *me_hel_dev, void *stream);
+
+/* Status of the device-side work issued so far for p on stream: synchronises
+ * the stream, returns MG_ERR_DEVICE_TIMEOUT (and clears it) when a bounded
+ * wait inside a kernel gave up since the last call (the kernel then wrote no
+ * valid result for the affected events), MG_ERR_CUDA on a CUDA error, else
+ * MG_OK. */
+int mg_device_status(mg_process *p, void *stream);
 
 /* Launch shape: threads per event (1..32, power of two) and threads per
  * block (multiple of 32, <= 1024).  0 keeps the current value. */

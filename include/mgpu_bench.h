@@ -17,6 +17,13 @@ extern "C" {
  * a negative mgpu status (MG_ERR_CUDA on a CUDA failure). */
 int mg_probe_fp64_peak(int blocks, int iters, int reps, double *flops_out);
 
+/* Test hook for the bounded waits of the tensor-core colour sum: every CTA's
+ * operand barrier then expects extra_bytes more than its copies deliver, so
+ * the wait runs out (about a second), the kernel records a timeout and
+ * returns; mg_device_status reports MG_ERR_DEVICE_TIMEOUT.  0 disables. */
+struct mg_process;
+int mg_debug_inject_stall(struct mg_process *p, unsigned int extra_bytes);
+
 #ifdef __cplusplus
 }
 #endif

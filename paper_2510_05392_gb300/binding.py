@@ -64,6 +64,10 @@ _SIGS = {
     "mg_process_destroy": ([_VP], None),
     "mg_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "mg_last_cuda_error": ([], ctypes.c_char_p),
+    "mg_device_status": ([_VP, _VP], ctypes.c_int),
+    "mg_debug_inject_stall": ([_VP, ctypes.c_uint], ctypes.c_int),
+    "mg_filter_helicities_noalloc": ([_VP, _VP, ctypes.c_int64, _VP, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "mg_probe_fp64_peak": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
 }
 
 
@@ -144,6 +148,10 @@ class Process:
         _check(lib().mg_sigmakin_hel(self._h, _ptr(momenta), momenta.shape[0], _ptr(out),
                                      _ptr(out_hel), _stream(stream)), "mg_sigmakin_hel")
         return out_hel
+
+    def device_status(self, stream=None) -> int:
+        """MG_OK or the status of the device-side work issued so far (syncs)."""
+        return lib().mg_device_status(self._h, _stream(stream))
 
     def set_launch(self, threads_per_event=0, block=0):
         _check(lib().mg_set_launch(self._h, threads_per_event, block), "mg_set_launch")

@@ -1,6 +1,7 @@
 // Host runtime behind the C ABI declared in include/mgpu.h: process
 // registry, device tables, argument checks, helicity filtering and the
 // launch of the diagram kernel.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -27,6 +28,16 @@ struct mg_process {
     uint8_t mask[256];
     int tpe, block;      // launch shape
     double factor;
+    // mixed precision: tensor-core colour sum (precision == MG_MIXED_BF16)
+    int kp, np;                  // padded colour counts (K per piece, N)
+    __nv_bfloat16 *d_cmat;       // [2*np][kp] BF16, D*C = hi + lo
+    __nv_bfloat16 *d_jbuf;       // jamp rows of one chunk, [rows][3*kp] BF16
+    long long jbuf_rows;
+    int jbuf_nunits;             // unit count the buffer's padding was zeroed for
+    double *d_part;              // partial colour sums of one chunk
+    long long part_len;
+    int *d_err;                  // device error word of the bounded waits
+    uint32_t debug_extra_tx;     // test hook: extra bytes the TMA barrier expects
 };
 
 namespace {
@@ -96,6 +107,10 @@ void free_proc(mg_process *p) {
     cudaFree(p->d_scat);
     cudaFree(p->d_cup);
     cudaFree(p->d_units);
+    cudaFree(p->d_cmat);
+    cudaFree(p->d_jbuf);
+    cudaFree(p->d_part);
+    cudaFree(p->d_err);
     free(p);
 }
 
@@ -126,6 +141,43 @@ int set_hel_list(mg_process *p, const uint8_t *mask) {
     p->nunits = nu;
     p->ngood = ngood;
     return MG_OK;
+}
+
+// Tensor-core colour sum set-up: padded sizes and the BF16 colour matrix
+// D*C = C_hi + C_lo (both parts exact in BF16; checked).
+int setup_mixed(mg_process *p) {
+    const mg_proc_table *t = p->tab;
+    const int nc = t->ncolor;
+    if (nc > 128) return MG_ERR_UNSUPPORTED;  // tiles hold up to 128 colour flows
+    p->kp = 64 * ((nc + 63) / 64);
+    p->np = 16 * ((nc + 15) / 16);
+    const size_t n = (size_t)2 * p->np * p->kp;
+    __nv_bfloat16 *h = (__nv_bfloat16 *)calloc(n, sizeof(__nv_bfloat16));
+    if (!h) return MG_ERR_NO_MEMORY;
+    for (int i = 0; i < nc; i++)
+        for (int j = 0; j < nc; j++) {
+            const double c = (double)t->chat[i * nc + j];
+            const __nv_bfloat16 hi = __float2bfloat16_rn((float)c);
+            const double rem = c - (double)__bfloat162float(hi);
+            const __nv_bfloat16 lo = __float2bfloat16_rn((float)rem);
+            if ((double)__bfloat162float(hi) + (double)__bfloat162float(lo) != c) {
+                free(h);
+                return MG_ERR_UNSUPPORTED;
+            }
+            h[(size_t)i * p->kp + j] = hi;
+            h[(size_t)(p->np + i) * p->kp + j] = lo;
+        }
+    cudaError_t e = cudaMalloc(&p->d_cmat, n * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_cmat, h, n * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice);
+    free(h);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? MG_ERR_NO_MEMORY : cuda_fail(e);
+    return MG_OK;
+}
+
+int pow2_at_least(int x) {
+    int v = 1;
+    while (v < x) v <<= 1;
+    return v;
 }
 
 int default_tpe(int npar) {
@@ -171,7 +223,6 @@ int mg_process_create(const char *process, const mg_params *params, mg_process *
     if (!(par.mt > 0.0) || !(par.wt >= 0.0) || !(par.alphas > 0.0)) return MG_ERR_BAD_ARG;
     if (par.hel_mode != MG_HEL_FILTERED && par.hel_mode != MG_HEL_ALL) return MG_ERR_BAD_ARG;
     if (par.precision != MG_FP64 && par.precision != MG_MIXED_BF16) return MG_ERR_BAD_ARG;
-    if (par.precision == MG_MIXED_BF16) return MG_ERR_UNSUPPORTED;
     int ntab = 0;
     const mg_proc_table *tabs = mg_tables(&ntab);
     const std::string want = normalise(process);
@@ -224,6 +275,12 @@ int mg_process_create(const char *process, const mg_params *params, mg_process *
     if (t->nscat > 0)
         TRY(cudaMemcpy(p->d_scat, t->scat, sizeof(int32_t) * t->nscat, cudaMemcpyHostToDevice));
     TRY(cudaMemcpy(p->d_cup, cup, sizeof(double) * ntri, cudaMemcpyHostToDevice));
+    TRY(cudaMalloc(&p->d_err, sizeof(int)));
+    TRY(cudaMemset(p->d_err, 0, sizeof(int)));
+    if (par.precision == MG_MIXED_BF16) {
+        st = setup_mixed(p);
+        if (st != MG_OK) goto fail;
+    }
 #undef TRY
     free(cup);
     if (par.hel_mode == MG_HEL_ALL) {
@@ -333,6 +390,57 @@ int mg_filter_helicities(mg_process *p, const double *mom, int64_t n, void *stre
     return MG_OK;
 }
 
+// Mixed precision: per chunk of events, the diagram kernel writes the jamps
+// as BF16 GEMM rows, the tensor-core kernel forms the colour sums, and a small
+// kernel adds each event's partial sums.  The chunk workspace is allocated on
+// the first call and kept (the library owns it; freed by destroy).
+static int sigmakin_mixed(mg_process *p, const double *mom, int64_t nevt, double *me, int tpe,
+                          cudaStream_t s) {
+    const int nup = pow2_at_least(p->nunits);
+    const int cpe = 8 * nup;                                  // GEMM rows per event
+    const long long row_bytes = 3LL * p->kp * 2;
+    const long long ev_align = cpe < 128 ? 128 / cpe : 1;     // events per whole tile
+    long long chunk = (1LL << 31) / (row_bytes * cpe);        // <= 2 GiB of jamp rows
+    chunk = chunk / ev_align * ev_align;
+    if (chunk < ev_align) chunk = ev_align;
+    if (chunk > nevt) chunk = (nevt + ev_align - 1) / ev_align * ev_align;
+    const long long rows = (chunk * cpe + 127) / 128 * 128;
+    const int per_event = cpe >= 128 ? cpe / 128 : 1;
+    const long long parts = rows / 128 * (cpe >= 128 ? 1 : 128 / cpe);
+    if (rows > p->jbuf_rows) {
+        cudaFree(p->d_jbuf);
+        p->d_jbuf = nullptr;
+        p->jbuf_rows = 0;
+        cudaError_t e = cudaMalloc(&p->d_jbuf, rows * row_bytes);
+        if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? MG_ERR_NO_MEMORY : cuda_fail(e);
+        p->jbuf_rows = rows;
+        p->jbuf_nunits = -1;
+    }
+    if (p->jbuf_nunits != p->nunits) {  // rows of padding units must read as zero
+        MG_CUDA(cudaMemsetAsync(p->d_jbuf, 0, p->jbuf_rows * row_bytes, s));
+        p->jbuf_nunits = p->nunits;
+    }
+    if (parts > p->part_len) {
+        cudaFree(p->d_part);
+        p->d_part = nullptr;
+        p->part_len = 0;
+        cudaError_t e = cudaMalloc(&p->d_part, parts * sizeof(double));
+        if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? MG_ERR_NO_MEMORY : cuda_fail(e);
+        p->part_len = parts;
+    }
+    const mg_dev_proc dp = dev_view(p);
+    for (long long e0 = 0; e0 < nevt; e0 += chunk) {
+        const long long n = (nevt - e0 < chunk) ? nevt - e0 : chunk;
+        const long long used = (n * cpe + 127) / 128 * 128;
+        MG_CUDA(mg_launch_sigmakin(dp, mom + e0 * p->tab->npar * 4, n, p->d_units, p->nunits, tpe,
+                                   p->block, nullptr, nullptr, s, p->d_jbuf, p->kp, nup));
+        MG_CUDA(mg_launch_colorsum_tc(p->d_jbuf, used, p->kp, p->d_cmat, p->np, p->tab->ncolor,
+                                      cpe, p->debug_extra_tx, p->d_part, p->d_err, s));
+        MG_CUDA(mg_launch_event_sum(p->d_part, n, per_event, p->factor, me + e0, s));
+    }
+    return MG_OK;
+}
+
 static int sigmakin_impl(mg_process *p, const double *mom, int64_t nevt, double *me,
                          double *me_hel, void *stream) {
     if (!p) return MG_ERR_BAD_ARG;
@@ -353,6 +461,10 @@ static int sigmakin_impl(mg_process *p, const double *mom, int64_t nevt, double 
     }
     int tpe = p->tpe;
     while (tpe > 1 && tpe > p->nunits) tpe >>= 1;
+    if (p->par.precision == MG_MIXED_BF16) {
+        if (me_hel) return MG_ERR_UNSUPPORTED;
+        return sigmakin_mixed(p, mom, nevt, me, tpe, s);
+    }
     MG_CUDA(mg_launch_sigmakin(dev_view(p), mom, nevt, p->d_units, p->nunits, tpe, p->block, me,
                                me_hel, s));
     return MG_OK;
@@ -443,5 +555,25 @@ extern "C" int mg_filter_helicities_noalloc(mg_process *p, const double *mom, in
     st = set_hel_list(p, mask);
     if (st) return st;
     if (ngood_out) *ngood_out = p->ngood;
+    return MG_OK;
+}
+
+// ---------------------------------------------------------------------------
+extern "C" int mg_device_status(mg_process *p, void *stream) {
+    if (!p) return MG_ERR_BAD_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int h = 0;
+    MG_CUDA(cudaStreamSynchronize(s));
+    MG_CUDA(cudaMemcpy(&h, p->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) {
+        MG_CUDA(cudaMemset(p->d_err, 0, sizeof(int)));
+        return MG_ERR_DEVICE_TIMEOUT;
+    }
+    return MG_OK;
+}
+
+extern "C" int mg_debug_inject_stall(mg_process *p, unsigned int extra_bytes) {
+    if (!p) return MG_ERR_BAD_ARG;
+    p->debug_extra_tx = extra_bytes;
     return MG_OK;
 }

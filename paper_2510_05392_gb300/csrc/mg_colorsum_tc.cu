@@ -1,0 +1,322 @@
+// Colour sum on the tensor cores (tcgen05, sm_103a): the mixed-precision
+// variant of the paper's colour sum J^H C J = A^T C A + B^T C B (Sec. 3.3,
+// Eq. "jcj"; Sec. 3.4 runs it as one GEMM over all helicities).
+//
+// Columns.  Every real vector V (the real or the imaginary part of the jamps
+// of one event and helicity) is a GEMM row m of length ncolor, stored as
+// three BF16 pieces V = V_hi + V_mid + V_lo (about 24 significant bits), each
+// padded to KP colours:  jbuf[m][s*KP + c], s = hi, mid, lo.
+// The colour matrix D*C (integers, not all exact in BF16 for 120 flows) is
+// split C_hat = C_hi + C_lo, both exact in BF16:  cmat[h*NP + n][c].
+//
+// One CTA computes Z = V C_hat^T for 128 columns (M = 128, N = NP colours,
+// K = KP per piece) with FP32 accumulation in tensor memory:
+//   Z = sum_{s in hi,mid,lo} V_s C_hi  +  sum_{s in hi,mid} V_s C_lo
+// (V_lo C_lo, relatively ~2^-24, is dropped), then each of the 128 epilogue
+// threads reads its row of Z from TMEM and forms sum_n V[m][n] Z[m][n] in
+// FP64 (V = hi + mid + lo from the same buffer).  Column sums are reduced per
+// event group in shared memory (fixed order) and written to part[].
+//
+// Operands reach shared memory by TMA (cp.async.bulk.tensor, 128-byte
+// swizzle, box 64 x rows); one elected thread issues tcgen05.mma and
+// tcgen05.commit; every wait on an mbarrier is bounded: on timeout the CTA
+// records MG_TC_ERR_TIMEOUT in *err, waits (bounded) for its copies, frees its
+// tensor memory and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mg_internal.h"
+
+namespace {
+
+constexpr int TC_M = 128;            // GEMM rows (columns of V) per CTA
+constexpr int TC_KCHUNK = 64;        // BF16 elements per 128-byte swizzle row
+constexpr long long TC_WAIT_CYCLES = 1LL << 31;  // ~1 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait: false when the limit ran out
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > limit) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor (tcgen05): K-major operand written by TMA
+// with the 128-byte swizzle; 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);      // start address      [0,14)
+    d |= (uint64_t)1 << 16;                         // leading byte offset (unused, swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;               // stride byte offset  [32,46)
+    d |= (uint64_t)1 << 46;                         // descriptor version  [46,48)
+    d |= (uint64_t)2 << 61;                         // 128-byte swizzle    [61,64)
+    return d;
+}
+
+// Instruction descriptor: kind::f16 with BF16 A/B, FP32 D, both K-major.
+__host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
+    return (1u << 4)                 // D format F32
+           | (1u << 7)               // A format BF16
+           | (1u << 10)              // B format BF16
+           | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(128, 1)
+    k_colorsum_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                  const __nv_bfloat16 *__restrict__ jbuf, int kp, int np, int ncolor, int cpe,
+                  int tmem_cols, uint32_t extra_tx, double *__restrict__ part, int *__restrict__ err) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int kc_n = kp / TC_KCHUNK;
+    const int a_chunk = TC_M * 128;   // bytes per A chunk (128 rows x 128 B)
+    const int b_chunk = np * 128;     // bytes per B chunk
+    unsigned char *sA = smem;                                  // [3][kc_n] chunks
+    unsigned char *sB = sA + 3 * kc_n * a_chunk;               // [2][kc_n] chunks
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sB + 2 * kc_n * b_chunk);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2);
+    double *colsum = reinterpret_cast<double *>(bars + 4);
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const long long m0 = (long long)blockIdx.x * TC_M;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 32) {
+        mbar_init(&bars[0], 1);  // operands landed
+        mbar_init(&bars[1], 1);  // accumulator ready
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    const uint32_t bytes = (uint32_t)(3 * kc_n * a_chunk + 2 * kc_n * b_chunk);
+    bool ok = true;
+    if (tid == 0) {
+        mbar_expect_tx(&bars[0], bytes + extra_tx);
+        for (int s = 0; s < 3; s++)
+            for (int kc = 0; kc < kc_n; kc++)
+                tma_load_2d(sA + (s * kc_n + kc) * a_chunk, &tmA, s * kp + kc * TC_KCHUNK, (int)m0,
+                            &bars[0]);
+        for (int h = 0; h < 2; h++)
+            for (int kc = 0; kc < kc_n; kc++)
+                tma_load_2d(sB + (h * kc_n + kc) * b_chunk, &tmB, kc * TC_KCHUNK, h * np, &bars[0]);
+        ok = mbar_wait(&bars[0], 0, TC_WAIT_CYCLES);
+        if (ok) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t idesc = instr_desc(TC_M, np);
+            uint32_t acc = 0;
+            // V_{hi,mid,lo} C_hi, then V_{hi,mid} C_lo; K = 16 per instruction
+            for (int pass = 0; pass < 2; pass++) {
+                const int nsplit = pass == 0 ? 3 : 2;
+                for (int s = 0; s < nsplit; s++)
+                    for (int kc = 0; kc < kc_n; kc++) {
+                        const uint32_t a0 = smem_u32(sA + (s * kc_n + kc) * a_chunk);
+                        const uint32_t b0 = smem_u32(sB + (pass * kc_n + kc) * b_chunk);
+                        for (int k = 0; k < TC_KCHUNK / 16; k++) {
+                            mma_bf16(tmem, smem_desc(a0 + 32 * k), smem_desc(b0 + 32 * k), idesc, acc);
+                            acc = 1;
+                        }
+                    }
+            }
+            mma_commit(&bars[1]);
+        } else {
+            atomicExch(err, MG_TC_ERR_TIMEOUT);
+            // let copies still in flight land before the CTA's memory goes away
+            mbar_wait(&bars[0], 0, TC_WAIT_CYCLES >> 2);
+        }
+    }
+    __syncthreads();
+    ok = (tid == 0) ? ok : true;
+    // every thread waits for the accumulator (bounded); a CTA whose loads timed
+    // out never commits, so its threads skip the wait through the flag below
+    __shared__ int s_failed;
+    if (tid == 0) s_failed = ok ? 0 : 1;
+    __syncthreads();
+    double acc = 0.0;
+    if (!s_failed) {
+        // warp-uniform decision: tcgen05.ld below is a warp-collective instruction
+        const bool landed = __all_sync(0xffffffffu, mbar_wait(&bars[1], 0, TC_WAIT_CYCLES));
+        if (!landed) {
+            atomicExch(err, MG_TC_ERR_TIMEOUT);
+        } else {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const __nv_bfloat16 *row = jbuf + (m0 + tid) * (long long)(3 * kp);
+            const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+            for (int c0 = 0; c0 < np; c0 += 16) {
+                uint32_t z[16];
+                tmem_ld16(lane_addr + (uint32_t)c0, z);
+#pragma unroll
+                for (int j = 0; j < 16; j++) {
+                    const int n = c0 + j;
+                    if (n < ncolor) {
+                        const float v = __bfloat162float(row[n]) + __bfloat162float(row[kp + n]) +
+                                        __bfloat162float(row[2 * kp + n]);
+                        acc = fma((double)v, (double)__uint_as_float(z[j]), acc);
+                    }
+                }
+            }
+        }
+    }
+    colsum[tid] = acc;
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    // fixed-order reduction of each event group of cpe columns inside the tile
+    const int gsize = cpe < TC_M ? cpe : TC_M;
+    const int ngroups = TC_M / gsize;
+    if (tid < ngroups) {
+        double s = 0.0;
+        for (int j = 0; j < gsize; j++) s += colsum[tid * gsize + j];
+        part[blockIdx.x * (long long)ngroups + tid] = s;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(tmem_cols)
+                     : "memory");
+    }
+}
+
+// me[e] = factor * (sum of the event's partial column sums), fixed order.
+__global__ void k_event_sum(const double *__restrict__ part, long long nevt, int per_event,
+                            double factor, double *__restrict__ me) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nevt) return;
+    double s = 0.0;
+    for (int j = 0; j < per_event; j++) s += part[e * per_event + j];
+    me[e] = s * factor;
+}
+
+typedef CUresult (*encode_tiled_fn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                    const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                    const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                    CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+encode_tiled_fn encode_fn() {
+    static encode_tiled_fn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<encode_tiled_fn>(p);
+    }
+    return fn;
+}
+
+// 2-D BF16 tensor map, row-major [rows][cols], box = box_rows x 64, 128B swizzle.
+bool make_map(CUtensorMap *m, const void *base, uint64_t rows, uint64_t cols, uint32_t box_rows) {
+    encode_tiled_fn f = encode_fn();
+    if (!f) return false;
+    const cuuint64_t dims[2] = {cols, rows};
+    const cuuint64_t strides[1] = {cols * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)TC_KCHUNK, box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return f(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box,
+             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+size_t mg_tc_smem_bytes(int kp, int np) {
+    const int kc_n = kp / TC_KCHUNK;
+    return 1024 + (size_t)3 * kc_n * TC_M * 128 + (size_t)2 * kc_n * np * 128 + 4 * 8 + TC_M * 8;
+}
+
+cudaError_t mg_launch_colorsum_tc(const __nv_bfloat16 *jbuf, long long ncols_alloc, int kp,
+                                  const __nv_bfloat16 *cmat, int np, int ncolor, int cpe,
+                                  uint32_t extra_tx, double *part, int *err, cudaStream_t stream) {
+    if (ncols_alloc % TC_M || kp % TC_KCHUNK || np % 16 || np > 256 || kp > 256)
+        return cudaErrorInvalidValue;
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, jbuf, (uint64_t)ncols_alloc, (uint64_t)3 * kp, TC_M)) return cudaErrorInvalidValue;
+    if (!make_map(&mb, cmat, (uint64_t)2 * np, (uint64_t)kp, (uint32_t)np)) return cudaErrorInvalidValue;
+    int tmem_cols = 32;
+    while (tmem_cols < np) tmem_cols <<= 1;
+    const size_t smem = mg_tc_smem_bytes(kp, np);
+    cudaError_t e = cudaFuncSetAttribute(k_colorsum_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    const long long grid = ncols_alloc / TC_M;
+    k_colorsum_tc<<<(unsigned)grid, TC_M, smem, stream>>>(ma, mb, jbuf, kp, np, ncolor, cpe,
+                                                           tmem_cols, extra_tx, part, err);
+    return cudaGetLastError();
+}
+
+cudaError_t mg_launch_event_sum(const double *part, long long nevt, int per_event, double factor,
+                                double *me, cudaStream_t stream) {
+    if (nevt <= 0) return cudaSuccess;
+    k_event_sum<<<(unsigned)((nevt + 255) / 256), 256, 0, stream>>>(part, nevt, per_event, factor, me);
+    return cudaGetLastError();
+}

@@ -60,14 +60,29 @@ typedef struct {
     double factor;                   // g^(2n) / (iden * D)
 } mg_dev_proc;
 
+#define MG_TC_ERR_TIMEOUT 1   // device error word: a bounded wait ran out
+
 #ifdef __cplusplus
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
-// Launchers (mg_kernels.cu).  All asynchronous on `stream`.
+// Launchers (mg_kernels.cu, mg_colorsum_tc.cu).  All asynchronous on `stream`.
 // units: work units (gluon-helicity configuration << 4 | mask of the good
 // (top, antitop) helicity combinations, bit 2*bt + btb), nunits of them.
+// jout != NULL: write the jamps as tensor-core GEMM rows (no FP64 colour sum,
+// me/me_hel unused); row index ((e * nunits_pad + unit) * 4 + v) * 2 + re/im.
 cudaError_t mg_launch_sigmakin(const mg_dev_proc &dp, const double *mom, int64_t nevt,
                                const int *units, int nunits, int tpe, int block, double *me,
-                               double *me_hel, cudaStream_t stream);
+                               double *me_hel, cudaStream_t stream, __nv_bfloat16 *jout = nullptr,
+                               int kp = 0, int nunits_pad = 0);
 cudaError_t mg_launch_helmask(const double *me_hel, int64_t n, int nhel, double rel,
                               unsigned char *mask, cudaStream_t stream);
+// tensor-core colour sum over ncols_alloc (multiple of 128) GEMM rows of jbuf
+// ([ncols][3*kp] BF16) with cmat ([2*np][kp] BF16: D*C split hi/lo); writes
+// one partial sum per event group of cpe rows (per 128-row tile if cpe >= 128)
+cudaError_t mg_launch_colorsum_tc(const __nv_bfloat16 *jbuf, long long ncols_alloc, int kp,
+                                  const __nv_bfloat16 *cmat, int np, int ncolor, int cpe,
+                                  uint32_t extra_tx, double *part, int *err, cudaStream_t stream);
+cudaError_t mg_launch_event_sum(const double *part, long long nevt, int per_event, double factor,
+                                double *me, cudaStream_t stream);
+size_t mg_tc_smem_bytes(int kp, int np);
 #endif

@@ -18,6 +18,7 @@
 // thread and reused by all of its helicities; gluon wavefunctions are shared
 // by the four top/antitop helicities of a unit (helicity recycling of the
 // FP64 work that does not depend on the top helicities).
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -108,7 +109,8 @@ __device__ __forceinline__ int helicity_index(int g, int bt, int btb) {
 template <int NG, int NSG, int NSF, int NC>
 __device__ void run_unit(const Kin<NG> &k, int g, const int4 *__restrict__ ops, int nops,
                          const int *__restrict__ scat, const double *__restrict__ cup, double mt,
-                         cx (*WG)[4], cx (*WF)[2][4], cx (*G0)[4], cx (*J)[NC], double *me4) {
+                         cx (*WG)[4], cx (*WF)[2][4], cx (*G0)[4], cx (*J)[NC], double *me4,
+                         bool colour_sum) {
     for (int v = 0; v < 4; v++)
         for (int c = 0; c < NC; c++) J[v][c] = mk(0.0, 0.0);
     for (int i = 0; i < nops; i++) {
@@ -205,6 +207,7 @@ __device__ void run_unit(const Kin<NG> &k, int g, const int4 *__restrict__ ops, 
                 break;
         }
     }
+    if (!colour_sum) return;
     // colour sum over the packed upper triangle (diagonal D*C_ii, off-diagonal
     // 2*D*C_ij), the four helicity combinations sharing each matrix entry
     double me[4] = {0.0, 0.0, 0.0, 0.0};
@@ -225,12 +228,46 @@ __device__ void run_unit(const Kin<NG> &k, int g, const int4 *__restrict__ ops, 
     for (int v = 0; v < 4; v++) me4[v] = me[v];
 }
 
+// Jamps of one unit as GEMM rows for the tensor-core colour sum: row
+// m = ((e * nunits_pad + iu) * 4 + v) * 2 + (0: real, 1: imaginary part),
+// each [3][kp] BF16 pieces hi, mid, lo with x ~= hi + mid + lo (the FP64 value
+// rounded to FP32, then split twice); colours >= NC and masked-out helicity
+// combinations are written as zeros.
+template <int NC>
+__device__ void write_jamp_rows(const cx (*J)[NC], int mask, __nv_bfloat16 *__restrict__ jout,
+                                long long row0, int kp) {
+    for (int v = 0; v < 4; v++) {
+        const bool on = (mask >> v) & 1;
+        for (int ri = 0; ri < 2; ri++) {
+            __nv_bfloat16 *row = jout + (row0 + 2 * v + ri) * (long long)(3 * kp);
+            for (int c0 = 0; c0 < kp; c0 += 8) {
+                __align__(16) __nv_bfloat16 hi[8], mid[8], lo[8];
+#pragma unroll
+                for (int q = 0; q < 8; q++) {
+                    const int c = c0 + q;
+                    double x = 0.0;
+                    if (on && c < NC) x = ri ? J[v][c].i : J[v][c].r;
+                    const float f = __double2float_rn(x);
+                    hi[q] = __float2bfloat16_rn(f);
+                    const float r1 = f - __bfloat162float(hi[q]);
+                    mid[q] = __float2bfloat16_rn(r1);
+                    lo[q] = __float2bfloat16_rn(r1 - __bfloat162float(mid[q]));
+                }
+                *reinterpret_cast<uint4 *>(row + c0) = *reinterpret_cast<const uint4 *>(hi);
+                *reinterpret_cast<uint4 *>(row + kp + c0) = *reinterpret_cast<const uint4 *>(mid);
+                *reinterpret_cast<uint4 *>(row + 2 * kp + c0) = *reinterpret_cast<const uint4 *>(lo);
+            }
+        }
+    }
+}
+
 template <int NG, int NSG, int NSF, int NC>
 __global__ void __launch_bounds__(256)
     k_sigmakin(const double *__restrict__ mom, long long nevt, const int4 *__restrict__ ops,
                int nops, const int *__restrict__ scat, const double *__restrict__ cup,
                const int *__restrict__ units, int nunits, int tpe, double mt, double wt,
-               double factor, double *__restrict__ me, double *__restrict__ me_hel) {
+               double factor, double *__restrict__ me, double *__restrict__ me_hel,
+               __nv_bfloat16 *__restrict__ jout, int kp, int nunits_pad) {
     constexpr int NPAR = NG + 2;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long e = t / tpe;
@@ -247,7 +284,11 @@ __global__ void __launch_bounds__(256)
             const int u = __ldg(units + iu);
             const int g = u >> 4, mask = u & 15;
             double me4[4];
-            run_unit<NG, NSG, NSF, NC>(k, g, ops, nops, scat, cup, mt, WG, WF, G0, J, me4);
+            run_unit<NG, NSG, NSF, NC>(k, g, ops, nops, scat, cup, mt, WG, WF, G0, J, me4, !jout);
+            if (jout) {
+                write_jamp_rows<NC>(J, mask, jout, (e * nunits_pad + iu) * 8, kp);
+                continue;
+            }
             for (int v = 0; v < 4; v++) {
                 if (!((mask >> v) & 1)) continue;
                 sum += me4[v];
@@ -278,7 +319,8 @@ __global__ void k_helmask(const double *__restrict__ mh, long long n, int nhel, 
 
 cudaError_t mg_launch_sigmakin(const mg_dev_proc &dp, const double *mom, int64_t nevt,
                                const int *units, int nunits, int tpe, int block, double *me,
-                               double *me_hel, cudaStream_t stream) {
+                               double *me_hel, cudaStream_t stream, __nv_bfloat16 *jout, int kp,
+                               int nunits_pad) {
     if (nevt <= 0) return cudaSuccess;
     const long long threads = (long long)nevt * tpe;
     const long long grid = (threads + block - 1) / block;
@@ -288,7 +330,7 @@ cudaError_t mg_launch_sigmakin(const mg_dev_proc &dp, const double *mom, int64_t
     case IDX:                                                                                    \
         k_sigmakin<NG, NSG, NSF, NC><<<(unsigned)grid, block, 0, stream>>>(                      \
             mom, nevt, reinterpret_cast<const int4 *>(dp.ops), dp.nops, dp.scat, dp.cup, units,   \
-            nunits, tpe, dp.mt, dp.wt, dp.factor, me, me_hel);                                   \
+            nunits, tpe, dp.mt, dp.wt, dp.factor, me, me_hel, jout, kp, nunits_pad);              \
         break;
         MG_PROC_LIST(MG_LAUNCH)
 #undef MG_LAUNCH

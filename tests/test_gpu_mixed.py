@@ -1,0 +1,89 @@
+"""GPU: the mixed-precision path (FP64 diagrams, tensor-core colour sum).
+
+Bound: per-event relative error <= 1e-6 against the FP64 oracle, the bound
+stated for the mixed colour sum (jamps in three BF16 pieces, colour matrix in
+two, FP32 accumulation on the tensor cores, FP64 epilogue).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_05392_gb300 import binding
+from paper_2510_05392_gb300 import phasespace as ps
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+MIXED_RTOL = 1e-6
+CASES = {0: (1000.0, 515), 1: (1500.0, 301), 2: (1500.0, 257), 3: (1500.0, 65)}
+
+
+def _events(ng, n, seed, sqrts):
+    kw = dict(ptmin=20.0, drmin=0.4) if ng else {}
+    return ps.generate(n, ng, sqrts, seed, **kw)
+
+
+def _mixed(ng, sqrts):
+    p = binding.Process("g g > t t~" + " g" * ng, precision=binding.MG_MIXED_BF16)
+    p.filter_helicities(torch.from_numpy(_events(ng, 16, 12345, sqrts)).cuda())
+    return p
+
+
+@pytest.mark.parametrize("ng", sorted(CASES))
+def test_mixed_colour_sum_within_bound(ng):
+    sqrts, n = CASES[ng]
+    mom = _events(ng, n, 3100 + ng, sqrts)
+    p = _mixed(ng, sqrts)
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    p.sigmakin(torch.from_numpy(mom).cuda(), out)
+    assert p.device_status() == binding.MG_OK
+    got = out.cpu().numpy()
+    ref = oracle.me(mom)
+    rel = np.abs(got / ref - 1)
+    print(f"ng={ng}: max rel {rel.max():.3e} median {np.median(rel):.3e}")
+    assert rel.max() <= MIXED_RTOL
+
+
+def test_mixed_matches_fp64_path_on_gpu():
+    sqrts, n = 1500.0, 200
+    mom = torch.from_numpy(_events(2, n, 3200, sqrts)).cuda()
+    a = binding.Process("g g > t t~ g g")
+    a.filter_helicities(torch.from_numpy(_events(2, 16, 12345, sqrts)).cuda())
+    b = _mixed(2, sqrts)
+    oa = torch.empty(n, dtype=torch.float64, device="cuda")
+    ob = torch.empty_like(oa)
+    a.sigmakin(mom, oa)
+    b.sigmakin(mom, ob)
+    torch.cuda.synchronize()
+    assert ((ob / oa - 1).abs().max().item()) <= MIXED_RTOL
+
+
+def test_mixed_rejects_per_helicity_and_large_colour_counts():
+    p = _mixed(1, 1500.0)
+    mom = torch.from_numpy(_events(1, 4, 1, 1500.0)).cuda()
+    with pytest.raises(binding.MGError) as e:
+        p.sigmakin_hel(mom, torch.empty(4, dtype=torch.float64, device="cuda"),
+                       torch.empty((4, 32), dtype=torch.float64, device="cuda"))
+    assert e.value.status == binding.MG_ERR_UNSUPPORTED
+    with pytest.raises(binding.MGError) as e:
+        binding.Process("g g > t t~ g g g g", precision=binding.MG_MIXED_BF16)
+    assert e.value.status == binding.MG_ERR_UNSUPPORTED
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    """A barrier that never completes (test hook) makes the tensor-core kernel
+    give up after its wait limit; the status is reported and the next call
+    works."""
+    sqrts = 1500.0
+    p = _mixed(2, sqrts)
+    mom_np = _events(2, 1, 3300, sqrts)           # one event = one 128-row tile
+    mom = torch.from_numpy(mom_np).cuda()
+    out = torch.empty(1, dtype=torch.float64, device="cuda")
+    L = binding.lib()
+    assert L.mg_debug_inject_stall(p.handle, 1024) == binding.MG_OK
+    p.sigmakin(mom, out)
+    assert p.device_status() == binding.MG_ERR_DEVICE_TIMEOUT
+    assert L.mg_debug_inject_stall(p.handle, 0) == binding.MG_OK
+    p.sigmakin(mom, out)
+    assert p.device_status() == binding.MG_OK
+    assert abs(out.item() / oracle.me(mom_np)[0] - 1) <= MIXED_RTOL

@@ -176,6 +176,65 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+BATCH_BLOCKS = [  # (process, ngluon_final, nevt): uneven blocks at sqrt(s) = 1500 GeV, cuts
+    ("g g > t t~", 0, 1048576), ("g g > t t~ g", 1, 262144),
+    ("g g > t t~ g g", 2, 65536), ("g g > t t~ g g g", 3, 16384)]
+
+
+def run_batch(args):
+    """Uneven multi-process batch in one persistent, graph-replayed launch
+    (autotuned), against the same blocks launched process by process."""
+    import torch
+    from paper_2510_05392_gb300 import binding, build
+    from paper_2510_05392_gb300 import phasespace as ps
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    blocks, total = [], 0
+    for proc, ng, n in BATCH_BLOCKS:
+        kw = dict(ptmin=20.0, drmin=0.4) if ng else {}
+        p = binding.Process(proc)
+        p.filter_helicities(torch.from_numpy(ps.generate(16, ng, 1500.0, TEST_SEED, **kw)).to(dev))
+        m = torch.from_numpy(ps.generate(n, ng, 1500.0, 20251005 + 4, **kw)).to(dev)
+        blocks.append((p, m, torch.empty(n, dtype=torch.float64, device=dev)))
+        total += n
+    b = binding.Batch(blocks)
+    tuned_ms = b.autotune(reps=1)
+    tpe, ctas = b.config()
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        b.run(stream)
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        b.run(stream)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    t_batch = ev0.elapsed_time(ev1) / 1e3
+    # the same blocks, one launch per process
+    ev0.record(stream)
+    for _ in range(args.steps):
+        for p, m, o in blocks:
+            p.sigmakin(m, o, stream)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    t_seq = ev0.elapsed_time(ev1) / 1e3
+    line = {
+        "metric": METRIC, "value": total * args.steps / t_batch, "unit": "events/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_batch / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (Philox4x32-10 + massive RAMBO, gluon cuts)",
+        "config": {"workload": "uneven_batch_4proc", "blocks": [[pr, n] for pr, _, n in BATCH_BLOCKS],
+                   "launch": "one persistent kernel per step, CUDA-graph replay",
+                   "autotuned": {"threads_per_event": tpe, "ctas_per_sm": ctas,
+                                 "tuning_ms_per_step": tuned_ms}},
+        "per_process_launches_events_per_s": total * args.steps / t_seq,
+        "gpu_launches": args.steps,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args):
     import torch
     from paper_2510_05392_gb300 import binding, build
@@ -196,7 +255,8 @@ def run_ours(args):
     mom_h = _events(name, nevt, first_candidate=rank * (1 << 40))
     mom = torch.from_numpy(mom_h).to(dev)
     out = torch.empty(nevt, dtype=torch.float64, device=dev)
-    p = binding.Process(proc)
+    prec = binding.MG_MIXED_BF16 if args.precision == "mixed" else binding.MG_FP64
+    p = binding.Process(proc, precision=prec)
     ngood = p.filter_helicities(torch.from_numpy(_test_events(name)).to(dev))
     if args.tpe or args.block:
         p.set_launch(args.tpe, args.block)
@@ -243,7 +303,11 @@ def run_ours(args):
     ms_step = 1e3 * t_dev / args.steps
 
     # algorithmic FP64 work of one launch
-    flops_launch = nevt * ngood * (info.flops_diagram + info.flops_colour)
+    # (mixed: the colour sum runs on the tensor cores, so only the diagram
+    # work is FP64; the timed step then also holds the colour-sum kernels,
+    # which makes the FP64 fraction a lower bound for the diagram kernel)
+    fp64_colour = info.flops_colour if args.precision == "fp64" else 0.0
+    flops_launch = nevt * ngood * (info.flops_diagram + fp64_colour)
     achieved = flops_launch / (statistics.mean(launch_ms) / 1e3)
 
     # end to end through the public API with pinned host buffers
@@ -275,6 +339,16 @@ def run_ours(args):
                "h2d_bytes_per_step": nevt * npar * 4 * 8, "d2h_bytes_per_step": nevt * 8}
         assert torch.isfinite(host_out).all().item()
 
+    accuracy = None
+    if rank == 0 and args.check > 0:
+        import numpy as np
+        import oracle
+        got = out.cpu().numpy()
+        idx = np.unique(np.linspace(0, nevt - 1, args.check).astype(np.int64))
+        rel = np.abs(got[idx] / oracle.me(mom_h[idx]) - 1)
+        accuracy = {"events_checked": int(len(idx)), "max_rel_err": float(rel.max()),
+                    "median_rel_err": float(np.median(rel)), "against": "CPU oracle (FP64)"}
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         v, cores, dt = cpu_baseline(name, args.cpu_sample)
@@ -286,10 +360,11 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic (Philox4x32-10 + massive RAMBO, gluon cuts)",
+            "dtype": "f64" if args.precision == "fp64" else "f64+bf16x3",
+            "data": "synthetic (Philox4x32-10 + massive RAMBO, gluon cuts)",
             "config": {"workload": name, "process": proc, "nevt_per_gpu": nevt,
                        "sqrt_s_gev": sqrts, "cuts": "pT>20 GeV, dR>0.4 (final gluons)" if cuts else "none",
-                       "precision": "fp64", "ngood_helicities": ngood,
+                       "precision": args.precision, "ngood_helicities": ngood,
                        "l2": "flushed between timed launches (256 MiB write, untimed)",
                        "parallelism": f"dp{ws} (independent events per GPU)"},
             "roofline": {"bound": "alu", "achieved": achieved / 1e12,
@@ -303,6 +378,7 @@ def run_ours(args):
             "gpu_launches": args.steps,
             "clocks": clk,
             "cpu_baseline": cpu,
+            "accuracy": accuracy,
             "wall_s_timed": wall,
         }
         print(json.dumps(line), flush=True)
@@ -316,12 +392,15 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="ggttgg_524288", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="ggttgg_524288",
+                    choices=sorted(WORKLOADS) + ["uneven_batch_4proc"])
     ap.add_argument("--nevt", type=int, default=0, help="override events per GPU (profiling)")
     ap.add_argument("--tpe", type=int, default=0)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--cpu-sample", type=int, default=16384)
     ap.add_argument("--ref-sample", type=int, default=4096)
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--check", type=int, default=0, help="events checked against the oracle")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
@@ -330,6 +409,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "uneven_batch_4proc":
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -154,6 +154,33 @@ int mg_helicity_mask(const mg_process *p, uint8_t *mask_out);
 
 void mg_process_destroy(mg_process *p);
 
+/* ---- uneven multi-process batches in one persistent launch -------------
+ * Blocks of events of several FP64 processes (each filtered, <= 5 gluons)
+ * evaluated by one persistent kernel: warps take 32-slot chunks (slot =
+ * event x thread of that event) from an atomic counter, heaviest process
+ * first.  The paper has no batch API; it runs one process per application
+ * (Sec. 2.3) and replays repeated launches as CUDA graphs (Sec. 4.1).
+ *
+ * mg_batch_create records the blocks (device pointers momenta[i]
+ * [nevt[i]][npar_i][4] and me_out[i] [nevt[i]], owned by the caller and read
+ * on every run); mg_batch_run replays the launch as a CUDA graph (captured on
+ * the first run on a private stream, asynchronous on `stream` afterwards);
+ * mg_batch_autotune times the batch for several threads-per-event choices of
+ * every block and CTAs per SM (coordinate descent, `reps` launches each,
+ * synchronous) and keeps the fastest, writing its time to *best_ms_out;
+ * mg_batch_config reports the choice (tpe_out[nproc], in the caller's
+ * order).  mg_sigmakin_batch is the one-shot form (create, one launch,
+ * synchronise, destroy). */
+typedef struct mg_batch mg_batch;
+int mg_batch_create(int nproc, mg_process *const *procs, const double *const *momenta_dev,
+                    const int64_t *nevt, double *const *me_out_dev, mg_batch **out);
+int mg_batch_run(mg_batch *b, void *stream);
+int mg_batch_autotune(mg_batch *b, void *stream, int reps, double *best_ms_out);
+int mg_batch_config(const mg_batch *b, int *tpe_out, int *ctas_per_sm_out);
+void mg_batch_destroy(mg_batch *b);
+int mg_sigmakin_batch(int nproc, mg_process *const *procs, const double *const *momenta_dev,
+                      const int64_t *nevt, double *const *me_out_dev, void *stream);
+
 const char *mg_status_string(int status);
 
 /* Last CUDA error string seen by the library on this thread ("" if none). */

@@ -67,6 +67,12 @@ _SIGS = {
     "mg_device_status": ([_VP, _VP], ctypes.c_int),
     "mg_debug_inject_stall": ([_VP, ctypes.c_uint], ctypes.c_int),
     "mg_filter_helicities_noalloc": ([_VP, _VP, ctypes.c_int64, _VP, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "mg_batch_create": ([ctypes.c_int, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_VP), ctypes.POINTER(_VP)], ctypes.c_int),
+    "mg_batch_run": ([_VP, _VP], ctypes.c_int),
+    "mg_batch_autotune": ([_VP, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "mg_batch_config": ([_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "mg_batch_destroy": ([_VP], None),
+    "mg_sigmakin_batch": ([ctypes.c_int, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_VP), _VP], ctypes.c_int),
     "mg_probe_fp64_peak": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
 }
 
@@ -171,3 +177,46 @@ class Process:
         _check(lib().mg_helicity_mask(self._h, m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))),
                "mg_helicity_mask")
         return m
+
+
+class Batch:
+    """Owner of one mg_batch plan over (Process, momenta tensor, output tensor)
+    blocks; the tensors must stay alive while the plan is used."""
+
+    def __init__(self, blocks):
+        n = len(blocks)
+        self._keep = blocks
+        procs = (_VP * n)(*[p.handle for p, _, _ in blocks])
+        moms = (_VP * n)(*[m.data_ptr() for _, m, _ in blocks])
+        outs = (_VP * n)(*[o.data_ptr() for _, _, o in blocks])
+        nev = (ctypes.c_int64 * n)(*[m.shape[0] for _, m, _ in blocks])
+        self._h = _VP()
+        _check(lib().mg_batch_create(n, procs, moms, nev, outs, ctypes.byref(self._h)),
+               "mg_batch_create")
+        self.n = n
+
+    def run(self, stream=None):
+        _check(lib().mg_batch_run(self._h, _stream(stream)), "mg_batch_run")
+
+    def autotune(self, reps=2, stream=None) -> float:
+        ms = ctypes.c_double(0.0)
+        _check(lib().mg_batch_autotune(self._h, _stream(stream), reps, ctypes.byref(ms)),
+               "mg_batch_autotune")
+        return ms.value
+
+    def config(self):
+        t = (ctypes.c_int * self.n)()
+        c = ctypes.c_int(0)
+        _check(lib().mg_batch_config(self._h, t, ctypes.byref(c)), "mg_batch_config")
+        return list(t), c.value
+
+    def close(self):
+        if self._h:
+            lib().mg_batch_destroy(self._h)
+            self._h = _VP()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -14,31 +14,7 @@
 #include "mg_internal.h"
 #include "mgpu.h"
 
-struct mg_process {
-    const mg_proc_table *tab;
-    int table_index;
-    mg_params par;
-    int device;
-    int32_t *d_ops;
-    int32_t *d_scat;
-    double *d_cup;
-    int *d_units;        // work units (device): gluon config << 4 | top-helicity mask
-    int nunits;
-    int ngood;           // -1 until filtered
-    uint8_t mask[256];
-    int tpe, block;      // launch shape
-    double factor;
-    // mixed precision: tensor-core colour sum (precision == MG_MIXED_BF16)
-    int kp, np;                  // padded colour counts (K per piece, N)
-    __nv_bfloat16 *d_cmat;       // [2*np][kp] BF16, D*C = hi + lo
-    __nv_bfloat16 *d_jbuf;       // jamp rows of one chunk, [rows][3*kp] BF16
-    long long jbuf_rows;
-    int jbuf_nunits;             // unit count the buffer's padding was zeroed for
-    double *d_part;              // partial colour sums of one chunk
-    long long part_len;
-    int *d_err;                  // device error word of the bounded waits
-    uint32_t debug_extra_tx;     // test hook: extra bytes the TMA barrier expects
-};
+#include "mg_process.h"
 
 namespace {
 
@@ -400,8 +376,17 @@ static int sigmakin_mixed(mg_process *p, const double *mom, int64_t nevt, double
     const int cpe = 8 * nup;                                  // GEMM rows per event
     const long long row_bytes = 3LL * p->kp * 2;
     const long long ev_align = cpe < 128 ? 128 / cpe : 1;     // events per whole tile
-    long long chunk = (1LL << 31) / (row_bytes * cpe);        // <= 2 GiB of jamp rows
-    chunk = chunk / ev_align * ev_align;
+    // chunk: whole waves of the diagram kernel (a partial last wave per chunk
+    // idles SMs), at most 12 GiB of jamp rows
+    int nsm = 0, occ = 1;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess ||
+        mg_sigmakin_occupancy(p->table_index, p->block, &occ) != MG_OK)
+        return MG_ERR_CUDA;
+    long long wave = (long long)nsm * occ * p->block / tpe;
+    wave = (wave + ev_align - 1) / ev_align * ev_align;
+    const long long limit = (12LL << 30) / (row_bytes * cpe);
+    long long chunk = limit / wave * wave;
+    if (chunk < wave) chunk = limit / ev_align * ev_align;
     if (chunk < ev_align) chunk = ev_align;
     if (chunk > nevt) chunk = (nevt + ev_align - 1) / ev_align * ev_align;
     const long long rows = (chunk * cpe + 127) / 128 * 128;
@@ -559,6 +544,10 @@ extern "C" int mg_filter_helicities_noalloc(mg_process *p, const double *mom, in
 }
 
 // ---------------------------------------------------------------------------
+int mg_check_dev_ptr(const void *ptr, int device) { return check_dev_ptr(ptr, device); }
+int mg_cuda_fail(cudaError_t e) { return cuda_fail(e); }
+mg_dev_proc mg_dev_view(const mg_process *p) { return dev_view(p); }
+
 extern "C" int mg_device_status(mg_process *p, void *stream) {
     if (!p) return MG_ERR_BAD_ARG;
     cudaStream_t s = (cudaStream_t)stream;

@@ -62,6 +62,22 @@ typedef struct {
 
 #define MG_TC_ERR_TIMEOUT 1   // device error word: a bounded wait ran out
 
+// One process block of a multi-process batch (device copy read by the
+// persistent kernel).  Slots [slot_begin, slot_end) are event * tpe + thread,
+// padded to a multiple of 32 so that every warp works on one item.
+typedef struct {
+    const int32_t *ops;
+    const int32_t *scat;
+    const double *cup;
+    const int *units;
+    const double *mom;
+    double *me;
+    long long nevt;
+    long long slot_begin, slot_end;
+    double mt, wt, factor;
+    int nops, nunits, tpe, table_index;
+} mg_batch_item;
+
 #ifdef __cplusplus
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -85,4 +101,10 @@ cudaError_t mg_launch_colorsum_tc(const __nv_bfloat16 *jbuf, long long ncols_all
 cudaError_t mg_launch_event_sum(const double *part, long long nevt, int per_event, double factor,
                                 double *me, cudaStream_t stream);
 size_t mg_tc_smem_bytes(int kp, int np);
+// persistent multi-process kernel: counter reset + one launch of grid CTAs
+cudaError_t mg_launch_batch(const mg_batch_item *d_items, int nitems, unsigned long long *d_counter,
+                            long long total_slots, int grid, cudaStream_t stream);
+int mg_batch_ctas_per_sm(int *out);
+int mg_sigmakin_occupancy(int table_index, int block, int *ctas_per_sm);
+#define MG_BATCH_MAX_NGLUON 5   // processes the persistent kernel carries
 #endif

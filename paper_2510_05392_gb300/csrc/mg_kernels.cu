@@ -109,10 +109,10 @@ __device__ __forceinline__ int helicity_index(int g, int bt, int btb) {
 template <int NG, int NSG, int NSF, int NC>
 __device__ void run_unit(const Kin<NG> &k, int g, const int4 *__restrict__ ops, int nops,
                          const int *__restrict__ scat, const double *__restrict__ cup, double mt,
-                         cx (*WG)[4], cx (*WF)[2][4], cx (*G0)[4], cx (*J)[NC], double *me4,
+                         cx (*WG)[4], cx (*WF)[2][4], cx (*G0)[4], cx (*J)[4], double *me4,
                          bool colour_sum) {
-    for (int v = 0; v < 4; v++)
-        for (int c = 0; c < NC; c++) J[v][c] = mk(0.0, 0.0);
+    for (int c = 0; c < NC; c++)
+        for (int v = 0; v < 4; v++) J[c][v] = mk(0.0, 0.0);
     for (int i = 0; i < nops; i++) {
         const int4 a = __ldg(ops + 2 * i);
         const int4 b = __ldg(ops + 2 * i + 1);
@@ -188,16 +188,16 @@ __device__ void run_unit(const Kin<NG> &k, int g, const int4 *__restrict__ ops, 
                     const int j = e >> 2;
                     switch (e & 3) {
                         case 0:
-                            for (int v = 0; v < 4; v++) J[v][j] = J[v][j] + amp[v];
+                            for (int v = 0; v < 4; v++) J[j][v] = J[j][v] + amp[v];
                             break;
                         case 1:
-                            for (int v = 0; v < 4; v++) J[v][j] = J[v][j] - amp[v];
+                            for (int v = 0; v < 4; v++) J[j][v] = J[j][v] - amp[v];
                             break;
                         case 2:
-                            for (int v = 0; v < 4; v++) J[v][j] = J[v][j] + mk(-amp[v].i, amp[v].r);
+                            for (int v = 0; v < 4; v++) J[j][v] = J[j][v] + mk(-amp[v].i, amp[v].r);
                             break;
                         default:
-                            for (int v = 0; v < 4; v++) J[v][j] = J[v][j] + mk(amp[v].i, -amp[v].r);
+                            for (int v = 0; v < 4; v++) J[j][v] = J[j][v] + mk(amp[v].i, -amp[v].r);
                             break;
                     }
                 }
@@ -218,12 +218,12 @@ __device__ void run_unit(const Kin<NG> &k, int g, const int4 *__restrict__ ops, 
             const double cij = __ldg(c++);
 #pragma unroll
             for (int v = 0; v < 4; v++) {
-                zr[v] = fma(cij, J[v][j].r, zr[v]);
-                zi[v] = fma(cij, J[v][j].i, zi[v]);
+                zr[v] = fma(cij, J[j][v].r, zr[v]);
+                zi[v] = fma(cij, J[j][v].i, zi[v]);
             }
         }
 #pragma unroll
-        for (int v = 0; v < 4; v++) me[v] = fma(J[v][i].r, zr[v], fma(J[v][i].i, zi[v], me[v]));
+        for (int v = 0; v < 4; v++) me[v] = fma(J[i][v].r, zr[v], fma(J[i][v].i, zi[v], me[v]));
     }
     for (int v = 0; v < 4; v++) me4[v] = me[v];
 }
@@ -234,7 +234,7 @@ __device__ void run_unit(const Kin<NG> &k, int g, const int4 *__restrict__ ops, 
 // rounded to FP32, then split twice); colours >= NC and masked-out helicity
 // combinations are written as zeros.
 template <int NC>
-__device__ void write_jamp_rows(const cx (*J)[NC], int mask, __nv_bfloat16 *__restrict__ jout,
+__device__ void write_jamp_rows(const cx (*J)[4], int mask, __nv_bfloat16 *__restrict__ jout,
                                 long long row0, int kp) {
     for (int v = 0; v < 4; v++) {
         const bool on = (mask >> v) & 1;
@@ -246,7 +246,7 @@ __device__ void write_jamp_rows(const cx (*J)[NC], int mask, __nv_bfloat16 *__re
                 for (int q = 0; q < 8; q++) {
                     const int c = c0 + q;
                     double x = 0.0;
-                    if (on && c < NC) x = ri ? J[v][c].i : J[v][c].r;
+                    if (on && c < NC) x = ri ? J[c][v].i : J[c][v].r;
                     const float f = __double2float_rn(x);
                     hi[q] = __float2bfloat16_rn(f);
                     const float r1 = f - __bfloat162float(hi[q]);
@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(256)
         cx WG[NSG > 0 ? NSG : 1][4];
         cx WF[NSF > 0 ? NSF : 1][2][4];
         cx G0[4][4];
-        cx J[4][NC];
+        cx J[NC][4];
         for (int iu = s; iu < nunits; iu += tpe) {
             const int u = __ldg(units + iu);
             const int g = u >> 4, mask = u & 15;
@@ -298,6 +298,72 @@ __global__ void __launch_bounds__(256)
     }
     for (int o = tpe >> 1; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
     if (e < nevt && s == 0 && me) me[e] = sum * factor;
+}
+
+// ------------------------------------------------ multi-process batch ----
+// One slot of a batch item: event e = slot / tpe, thread s = slot % tpe of that
+// event.  All 32 lanes of a warp call this for the same item (the shuffles
+// below span the warp).  Kept out of line so that the persistent kernel's
+// stack frame is the largest of the carried processes, not their sum.
+template <int NG, int NSG, int NSF, int NC>
+__device__ __noinline__ void batch_slot(const mg_batch_item &it, long long slot) {
+    constexpr int NPAR = NG + 2;
+    const int tpe = it.tpe;
+    const long long e = slot / tpe;
+    const int s = (int)(slot - e * tpe);
+    double sum = 0.0;
+    if (e < it.nevt) {
+        Kin<NG> k;
+        kinematics<NG>(k, it.mom + e * (NPAR * 4), it.mt, it.wt);
+        cx WG[NSG > 0 ? NSG : 1][4];
+        cx WF[NSF > 0 ? NSF : 1][2][4];
+        cx G0[4][4];
+        cx J[NC][4];
+        const int4 *ops = reinterpret_cast<const int4 *>(it.ops);
+        for (int iu = s; iu < it.nunits; iu += tpe) {
+            const int u = __ldg(it.units + iu);
+            double me4[4];
+            run_unit<NG, NSG, NSF, NC>(k, u >> 4, ops, it.nops, it.scat, it.cup, it.mt, WG, WF, G0,
+                                       J, me4, true);
+            for (int v = 0; v < 4; v++)
+                if ((u >> v) & 1) sum += me4[v];
+        }
+    }
+    for (int o = tpe >> 1; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (e < it.nevt && s == 0) it.me[e] = sum * it.factor;
+}
+
+template <int NG, int NSG, int NSF, int NC>
+__device__ __forceinline__ void batch_dispatch(const mg_batch_item &it, long long slot) {
+    if constexpr (NG <= MG_BATCH_MAX_NGLUON) batch_slot<NG, NSG, NSF, NC>(it, slot);
+}
+
+// Persistent kernel: every warp repeatedly takes the next 32 slots from the
+// global counter until all items are done (no waits on other threads).
+__global__ void __launch_bounds__(128, 3)
+    k_batch(const mg_batch_item *__restrict__ items, int nitems,
+            unsigned long long *__restrict__ counter, long long total_slots) {
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(counter, 32ULL);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if ((long long)base >= total_slots) return;
+        int i = 0;
+        while (i + 1 < nitems && (long long)base >= items[i].slot_end) i++;
+        const mg_batch_item &it = items[i];
+        const long long slot = (long long)base + lane - it.slot_begin;
+        switch (it.table_index) {
+#define MG_BATCH_CASE(IDX, NG, NSG, NSF, NC) \
+    case IDX:                                \
+        batch_dispatch<NG, NSG, NSF, NC>(it, slot); \
+        break;
+            MG_PROC_LIST(MG_BATCH_CASE)
+#undef MG_BATCH_CASE
+            default:
+                break;
+        }
+    }
 }
 
 // Helicity filter rule: good[h] = any_e ( mh[e][h] > rel * max_h' mh[e][h'] ).
@@ -344,4 +410,41 @@ cudaError_t mg_launch_helmask(const double *me_hel, int64_t n, int nhel, double 
                               unsigned char *mask, cudaStream_t stream) {
     k_helmask<<<(nhel + 127) / 128, 128, 0, stream>>>(me_hel, n, nhel, rel, mask);
     return cudaGetLastError();
+}
+
+cudaError_t mg_launch_batch(const mg_batch_item *d_items, int nitems, unsigned long long *d_counter,
+                            long long total_slots, int grid, cudaStream_t stream) {
+    cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), stream);
+    if (e != cudaSuccess) return e;
+    if (total_slots <= 0) return cudaSuccess;
+    k_batch<<<grid, 128, 0, stream>>>(d_items, nitems, d_counter, total_slots);
+    return cudaGetLastError();
+}
+
+int mg_batch_ctas_per_sm(int *out) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch, 128, 0) != cudaSuccess)
+        return MG_ERR_CUDA;
+    *out = n;
+    return MG_OK;
+}
+
+// CTAs of the process's diagram kernel resident per SM at this block size.
+int mg_sigmakin_occupancy(int table_index, int block, int *ctas_per_sm) {
+    int n = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (table_index) {
+#define MG_OCC(IDX, NG, NSG, NSF, NC)                                                        \
+    case IDX:                                                                                \
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sigmakin<NG, NSG, NSF, NC>, \
+                                                          block, 0);                         \
+        break;
+        MG_PROC_LIST(MG_OCC)
+#undef MG_OCC
+        default:
+            break;
+    }
+    if (e != cudaSuccess) return MG_ERR_CUDA;
+    *ctas_per_sm = n > 0 ? n : 1;
+    return MG_OK;
 }

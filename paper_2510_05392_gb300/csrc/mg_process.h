@@ -1,0 +1,38 @@
+// The process handle behind the opaque mg_process of include/mgpu.h (shared
+// by the host runtime files).
+#pragma once
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "mg_internal.h"
+
+struct mg_process {
+    const mg_proc_table *tab;
+    int table_index;
+    mg_params par;
+    int device;
+    int32_t *d_ops;
+    int32_t *d_scat;
+    double *d_cup;
+    int *d_units;        // work units (device): gluon config << 4 | top-helicity mask
+    int nunits;
+    int ngood;           // -1 until filtered
+    uint8_t mask[256];
+    int tpe, block;      // launch shape
+    double factor;
+    // mixed precision: tensor-core colour sum (precision == MG_MIXED_BF16)
+    int kp, np;                  // padded colour counts (K per piece, N)
+    __nv_bfloat16 *d_cmat;       // [2*np][kp] BF16, D*C = hi + lo
+    __nv_bfloat16 *d_jbuf;       // jamp rows of one chunk, [rows][3*kp] BF16
+    long long jbuf_rows;
+    int jbuf_nunits;             // unit count the buffer's padding was zeroed for
+    double *d_part;              // partial colour sums of one chunk
+    long long part_len;
+    int *d_err;                  // device error word of the bounded waits
+    uint32_t debug_extra_tx;     // test hook: extra bytes the TMA barrier expects
+};
+
+// helpers of mg_api.cu used by the other host files
+int mg_check_dev_ptr(const void *ptr, int device);
+int mg_cuda_fail(cudaError_t e);
+mg_dev_proc mg_dev_view(const mg_process *p);

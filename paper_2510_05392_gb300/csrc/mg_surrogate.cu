@@ -1,0 +1,716 @@
+// MLP surrogate of log|M|^2 and the two-stage unweighting it drives.
+//
+// The paper has no learned component; this is the benchmark configuration's
+// surrogate pattern, the published scheme of rejection sampling with network
+// weight estimates (Danziger, Janssen, Schumann, Siegert 2022):
+//   features  x = s_ij / s over all particle pairs (FP64, rounded to BF16)
+//   network   z_1 = W_1 x + b_1, a = silu(z), ..., f = z_L;  sizes
+//             nin -> hidden (x nhidden, SiLU) -> 1; BF16 weights/activations,
+//             FP32 accumulation, FP32 master weights, Adam
+//   target    y = (log|M|^2 - mu) / sigma, MSE loss
+//   unweight  w_hat = exp(sigma f + mu) Phi; stage 1 keeps u1 < w_hat/w_hat_max;
+//             the exact FP64 matrix element is evaluated for those only;
+//             stage 2 keeps u2 < (w/w_hat)/r_max, w = |M|^2 Phi; weight
+//             max(1, w_hat/w_hat_max) * max(1, (w/w_hat)/r_max)
+// GEMMs use the warp-level BF16 tensor-core instructions (WMMA 16x16x16,
+// FP32 accumulate) with bias / SiLU / SiLU' fused into their epilogues; the
+// layers are small, so these kernels are launch- rather than pipe-bound.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <mma.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "mg_process.h"
+#include "mgpu.h"
+
+using namespace nvcuda;
+
+namespace {
+
+constexpr int SUR_MAXL = 8;
+constexpr int WM = 16;
+
+__device__ __forceinline__ float silu_f(float z) { return z / (1.0f + __expf(-z)); }
+__device__ __forceinline__ float dsilu_f(float z) {
+    const float s = 1.0f / (1.0f + __expf(-z));
+    return s * (1.0f + z * (1.0f - s));
+}
+
+// features: x[i][k] = s_ij / s for pairs i < j (k in pair order), zero padded
+__global__ void k_features(const double *__restrict__ mom, long long n, int npar, int nin,
+                           __nv_bfloat16 *__restrict__ x) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const double *p = mom + e * npar * 4;
+    const double P0 = p[0] + p[4], P1 = p[1] + p[5], P2 = p[2] + p[6], P3 = p[3] + p[7];
+    const double s = P0 * P0 - P1 * P1 - P2 * P2 - P3 * P3;
+    int k = 0;
+    for (int i = 0; i < npar; i++)
+        for (int j = i + 1; j < npar; j++) {
+            const double q0 = p[4 * i] + p[4 * j], q1 = p[4 * i + 1] + p[4 * j + 1];
+            const double q2 = p[4 * i + 2] + p[4 * j + 2], q3 = p[4 * i + 3] + p[4 * j + 3];
+            if (k < nin) x[e * nin + k] = __float2bfloat16_rn((float)((q0 * q0 - q1 * q1 - q2 * q2 - q3 * q3) / s));
+            k++;
+        }
+    for (; k < nin; k++) x[e * nin + k] = __float2bfloat16_rn(0.0f);
+}
+
+// Forward layer: Z[M][N] = A[M][K] W[N][K]^T + b; Aout = silu(Z) (or Z for
+// the output layer).  One warp per 16x16 tile of Z.
+__global__ void k_fwd(const __nv_bfloat16 *__restrict__ A, const __nv_bfloat16 *__restrict__ W,
+                      const float *__restrict__ b, int M, int N, int K, int act,
+                      float *__restrict__ Z, __nv_bfloat16 *__restrict__ Aout) {
+    __shared__ float tile[4][WM * WM];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t = blockIdx.x * 4 + warp;
+    const int tn = N / WM;
+    if (t >= (M / WM) * tn) return;
+    const int m0 = (t / tn) * WM, n0 = (t % tn) * WM;
+    wmma::fragment<wmma::accumulator, WM, WM, WM, float> c;
+    wmma::fill_fragment(c, 0.0f);
+    for (int k = 0; k < K; k += WM) {
+        wmma::fragment<wmma::matrix_a, WM, WM, WM, __nv_bfloat16, wmma::row_major> fa;
+        wmma::fragment<wmma::matrix_b, WM, WM, WM, __nv_bfloat16, wmma::col_major> fb;
+        wmma::load_matrix_sync(fa, A + (long long)m0 * K + k, K);
+        wmma::load_matrix_sync(fb, W + (long long)n0 * K + k, K);
+        wmma::mma_sync(c, fa, fb, c);
+    }
+    wmma::store_matrix_sync(tile[warp], c, WM, wmma::mem_row_major);
+    __syncwarp();
+    for (int q = lane; q < WM * WM; q += 32) {
+        const int r = q / WM, cc = q % WM;
+        const float z = tile[warp][q] + b[n0 + cc];
+        const long long o = (long long)(m0 + r) * N + n0 + cc;
+        if (Z) Z[o] = z;
+        if (Aout) Aout[o] = __float2bfloat16_rn(act ? silu_f(z) : z);
+    }
+}
+
+// Backward through a layer's input: dZprev[M][K] = (dZ[M][N] W[N][K]) *
+// silu'(Zprev).  One warp per 16x16 tile.
+__global__ void k_bwd_data(const __nv_bfloat16 *__restrict__ dZ, const __nv_bfloat16 *__restrict__ W,
+                           const float *__restrict__ Zprev, int M, int N, int K,
+                           __nv_bfloat16 *__restrict__ dZprev) {
+    __shared__ float tile[4][WM * WM];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t = blockIdx.x * 4 + warp;
+    const int tk = K / WM;
+    if (t >= (M / WM) * tk) return;
+    const int m0 = (t / tk) * WM, k0 = (t % tk) * WM;
+    wmma::fragment<wmma::accumulator, WM, WM, WM, float> c;
+    wmma::fill_fragment(c, 0.0f);
+    for (int n = 0; n < N; n += WM) {
+        wmma::fragment<wmma::matrix_a, WM, WM, WM, __nv_bfloat16, wmma::row_major> fa;
+        wmma::fragment<wmma::matrix_b, WM, WM, WM, __nv_bfloat16, wmma::row_major> fb;
+        wmma::load_matrix_sync(fa, dZ + (long long)m0 * N + n, N);
+        wmma::load_matrix_sync(fb, W + (long long)n * K + k0, K);
+        wmma::mma_sync(c, fa, fb, c);
+    }
+    wmma::store_matrix_sync(tile[warp], c, WM, wmma::mem_row_major);
+    __syncwarp();
+    for (int q = lane; q < WM * WM; q += 32) {
+        const int r = q / WM, cc = q % WM;
+        const long long o = (long long)(m0 + r) * K + k0 + cc;
+        dZprev[o] = __float2bfloat16_rn(tile[warp][q] * dsilu_f(Zprev[o]));
+    }
+}
+
+// Weight gradient: gW[N][K] = dZ[M][N]^T A[M][K] (FP32).  One warp per tile.
+__global__ void k_bwd_weight(const __nv_bfloat16 *__restrict__ dZ, const __nv_bfloat16 *__restrict__ A,
+                             int M, int N, int K, float *__restrict__ gW) {
+    const int warp = threadIdx.x >> 5;
+    const int t = blockIdx.x * 4 + warp;
+    const int tk = K / WM;
+    if (t >= (N / WM) * tk) return;
+    const int n0 = (t / tk) * WM, k0 = (t % tk) * WM;
+    wmma::fragment<wmma::accumulator, WM, WM, WM, float> c;
+    wmma::fill_fragment(c, 0.0f);
+    for (int m = 0; m < M; m += WM) {
+        wmma::fragment<wmma::matrix_a, WM, WM, WM, __nv_bfloat16, wmma::col_major> fa;
+        wmma::fragment<wmma::matrix_b, WM, WM, WM, __nv_bfloat16, wmma::row_major> fb;
+        wmma::load_matrix_sync(fa, dZ + (long long)m * N + n0, N);
+        wmma::load_matrix_sync(fb, A + (long long)m * K + k0, K);
+        wmma::mma_sync(c, fa, fb, c);
+    }
+    wmma::store_matrix_sync(gW + (long long)n0 * K + k0, c, K, wmma::mem_row_major);
+}
+
+// gb[n] = sum_m dZ[m][n]
+__global__ void k_bias_grad(const __nv_bfloat16 *__restrict__ dZ, int M, int N, float *__restrict__ gb) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    float s = 0.0f;
+    for (int m = 0; m < M; m++) s += __bfloat162float(dZ[(long long)m * N + n]);
+    gb[n] = s;
+}
+
+// Output-layer loss gradient: dZ[m][0] = 2 (f_m - y_m) / M (other padded
+// columns 0); per-block partial sums of the squared error.
+__global__ void k_loss(const float *__restrict__ Zout, int M, int N, const float *__restrict__ y,
+                       __nv_bfloat16 *__restrict__ dZ, double *__restrict__ part) {
+    __shared__ double red[256];
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    double se = 0.0;
+    if (m < M) {
+        const float d = Zout[(long long)m * N] - y[m];
+        se = (double)d * d;
+        dZ[(long long)m * N] = __float2bfloat16_rn(2.0f * d / M);
+        for (int c = 1; c < N; c++) dZ[(long long)m * N + c] = __float2bfloat16_rn(0.0f);
+    }
+    red[threadIdx.x] = se;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+// Adam on FP32 master parameters (rows >= nrow_real of a padded output layer
+// stay zero: their gradients are zero), BF16 copy refreshed.
+__global__ void k_adam(float *__restrict__ p, float *__restrict__ m, float *__restrict__ v,
+                       const float *__restrict__ g, __nv_bfloat16 *__restrict__ p16, long long n,
+                       float lr, float b1, float b2, float eps, float c1, float c2) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float w = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    p[i] = w;
+    if (p16) p16[i] = __float2bfloat16_rn(w);
+}
+
+// target: y = (log me - mu) / sigma, with mu/sigma from k_logstats
+__global__ void k_target(const double *__restrict__ me, long long n, const double *__restrict__ ms,
+                         float *__restrict__ y) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = (float)((log(me[i]) - ms[0]) / ms[1]);
+}
+
+// mean and standard deviation of log(me) (single block, fixed order)
+__global__ void k_logstats(const double *__restrict__ me, long long n, double *__restrict__ ms) {
+    __shared__ double s1[256], s2[256];
+    double a = 0.0, b = 0.0;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+        const double l = log(me[i]);
+        a += l;
+        b += l * l;
+    }
+    s1[threadIdx.x] = a;
+    s2[threadIdx.x] = b;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            s1[threadIdx.x] += s1[threadIdx.x + s];
+            s2[threadIdx.x] += s2[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double mu = s1[0] / n;
+        const double var = s2[0] / n - mu * mu;
+        ms[0] = mu;
+        ms[1] = var > 0 ? sqrt(var) : 1.0;
+    }
+}
+
+// log|M|^2 prediction: sigma f + mu
+__global__ void k_pred(const float *__restrict__ Zout, int N, long long n, const double *__restrict__ ms,
+                       double *__restrict__ out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = ms[1] * (double)Zout[i * N] + ms[0];
+}
+
+// stage 1: w_hat = exp(logme_hat) Phi, flag u1 < w_hat / w_hat_max; block counts
+__global__ void k_stage1(const double *__restrict__ logme_hat, const double *__restrict__ phi,
+                         const double *__restrict__ u1, long long n, double what_max,
+                         double *__restrict__ what, unsigned char *__restrict__ flag,
+                         int *__restrict__ bcount) {
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const double w = exp(logme_hat[i]) * phi[i];
+        what[i] = w;
+        const unsigned char f = u1[i] < w / what_max;
+        flag[i] = f;
+        if (f) atomicAdd(&cnt, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) bcount[blockIdx.x] = cnt;
+}
+
+// exclusive scan of block counts (single block, fixed order)
+__global__ void k_scan(int *__restrict__ bcount, int nb, long long *__restrict__ total) {
+    if (threadIdx.x != 0) return;
+    long long s = 0;
+    for (int b = 0; b < nb; b++) {
+        const int c = bcount[b];
+        bcount[b] = (int)s;
+        s += c;
+    }
+    *total = s;
+}
+
+// ordered compaction of stage-1 survivors; gathers their momenta
+__global__ void k_compact(const unsigned char *__restrict__ flag, const int *__restrict__ boff,
+                          long long n, const double *__restrict__ mom, int npar,
+                          long long *__restrict__ idx, double *__restrict__ mom_out) {
+    __shared__ int pos[1024];
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int f = (i < n) ? flag[i] : 0;
+    pos[threadIdx.x] = f;
+    __syncthreads();
+    if (threadIdx.x == 0) {  // fixed-order prefix inside the block
+        int s = 0;
+        for (int t = 0; t < (int)blockDim.x; t++) {
+            const int v = pos[t];
+            pos[t] = s;
+            s += v;
+        }
+    }
+    __syncthreads();
+    if (f) {
+        const long long o = boff[blockIdx.x] + pos[threadIdx.x];
+        idx[o] = i;
+        for (int k = 0; k < npar * 4; k++) mom_out[o * npar * 4 + k] = mom[i * npar * 4 + k];
+    }
+}
+
+// stage 2 on the survivors: keep u2 < (w / w_hat) / r_max; weights
+__global__ void k_stage2(const long long *__restrict__ idx, const double *__restrict__ me_exact,
+                         long long m, const double *__restrict__ phi, const double *__restrict__ what,
+                         const double *__restrict__ u2, double what_max, double r_max,
+                         unsigned char *__restrict__ accept, double *__restrict__ weight) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= m) return;
+    const long long i = idx[k];
+    const double w = me_exact[k] * phi[i];
+    const double r = w / what[i];
+    const bool a = u2[i] < r / r_max;
+    accept[i] = a;
+    const double w1 = what[i] / what_max;
+    weight[i] = a ? fmax(1.0, w1) * fmax(1.0, r / r_max) : 0.0;
+}
+
+}  // namespace
+
+struct mg_surrogate {
+    int nl;                      // linear layers
+    int in[SUR_MAXL], out[SUR_MAXL], outp[SUR_MAXL];   // sizes (outp: padded to 16)
+    float *W[SUR_MAXL], *b[SUR_MAXL], *gW[SUR_MAXL], *gb[SUR_MAXL];
+    float *mW[SUR_MAXL], *vW[SUR_MAXL], *mb[SUR_MAXL], *vb[SUR_MAXL];
+    __nv_bfloat16 *W16[SUR_MAXL];
+    int t;                       // Adam steps taken
+    int bmax;                    // rows per forward/backward chunk
+    __nv_bfloat16 *A[SUR_MAXL + 1];  // activations (A[0] = features)
+    float *Z[SUR_MAXL];
+    __nv_bfloat16 *dZ[SUR_MAXL];
+    double *ms;                  // mu, sigma of log|M|^2 (device)
+    double *part;                // loss partial sums
+    float *y;                    // standardised targets of a chunk
+};
+
+namespace {
+
+int sur_fail(cudaError_t e) { return e == cudaErrorMemoryAllocation ? MG_ERR_NO_MEMORY : mg_cuda_fail(e); }
+
+#define SCHECK(x)                                   \
+    do {                                            \
+        cudaError_t _e = (x);                       \
+        if (_e != cudaSuccess) return sur_fail(_e); \
+    } while (0)
+
+void free_sur(mg_surrogate *s) {
+    if (!s) return;
+    for (int l = 0; l < SUR_MAXL; l++) {
+        cudaFree(s->W[l]); cudaFree(s->b[l]); cudaFree(s->gW[l]); cudaFree(s->gb[l]);
+        cudaFree(s->mW[l]); cudaFree(s->vW[l]); cudaFree(s->mb[l]); cudaFree(s->vb[l]);
+        cudaFree(s->W16[l]); cudaFree(s->Z[l]); cudaFree(s->dZ[l]);
+    }
+    for (int l = 0; l <= SUR_MAXL; l++) cudaFree(s->A[l]);
+    cudaFree(s->ms); cudaFree(s->part); cudaFree(s->y);
+    delete s;
+}
+
+int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
+
+// forward pass over rows [0, M) of s->A[0]
+int forward(mg_surrogate *s, int M, cudaStream_t st) {
+    for (int l = 0; l < s->nl; l++) {
+        const int tiles = (M / WM) * (s->outp[l] / WM);
+        const bool last = (l == s->nl - 1);
+        k_fwd<<<blocks_for(tiles, 4), 128, 0, st>>>(s->A[l], s->W16[l], s->b[l], M, s->outp[l],
+                                                   s->in[l], last ? 0 : 1, s->Z[l],
+                                                   last ? nullptr : s->A[l + 1]);
+    }
+    SCHECK(cudaGetLastError());
+    return MG_OK;
+}
+
+// backward pass (needs forward + k_loss): fills gW, gb
+int backward(mg_surrogate *s, int M, cudaStream_t st) {
+    for (int l = s->nl - 1; l >= 0; l--) {
+        const int tiles_w = (s->outp[l] / WM) * (s->in[l] / WM);
+        k_bwd_weight<<<blocks_for(tiles_w, 4), 128, 0, st>>>(s->dZ[l], s->A[l], M, s->outp[l],
+                                                            s->in[l], s->gW[l]);
+        k_bias_grad<<<blocks_for(s->outp[l], 128), 128, 0, st>>>(s->dZ[l], M, s->outp[l], s->gb[l]);
+        if (l > 0) {
+            const int tiles_d = (M / WM) * (s->in[l] / WM);
+            k_bwd_data<<<blocks_for(tiles_d, 4), 128, 0, st>>>(s->dZ[l], s->W16[l], s->Z[l - 1], M,
+                                                              s->outp[l], s->in[l], s->dZ[l - 1]);
+        }
+    }
+    SCHECK(cudaGetLastError());
+    return MG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mg_sur_create(int nin, int hidden, int nhidden, uint64_t seed, int bmax, mg_surrogate **out) {
+    if (!out || nin < 1 || nin % 16 || hidden < 16 || hidden % 16 || nhidden < 1 ||
+        nhidden + 1 > SUR_MAXL || bmax < 16 || bmax % 16)
+        return MG_ERR_BAD_ARG;
+    *out = nullptr;
+    mg_surrogate *s = new mg_surrogate();
+    memset(s, 0, sizeof(*s));
+    s->nl = nhidden + 1;
+    s->bmax = bmax;
+    for (int l = 0; l < s->nl; l++) {
+        s->in[l] = (l == 0) ? nin : hidden;
+        s->out[l] = (l == s->nl - 1) ? 1 : hidden;
+        s->outp[l] = (s->out[l] + WM - 1) / WM * WM;
+    }
+    // Glorot-uniform initial weights from a seeded generator (host), biases 0
+    uint64_t st = seed * 6364136223846793005ULL + 1442695040888963407ULL;
+    auto uni = [&]() {
+        st = st * 6364136223846793005ULL + 1442695040888963407ULL;
+        return ((st >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    };
+    int rc = MG_OK;
+    for (int l = 0; l < s->nl && rc == MG_OK; l++) {
+        const size_t nw = (size_t)s->outp[l] * s->in[l], nb = s->outp[l];
+        std::vector<float> w(nw, 0.0f);
+        const double lim = sqrt(6.0 / (s->in[l] + s->out[l]));
+        for (int r = 0; r < s->out[l]; r++)
+            for (int c = 0; c < s->in[l]; c++) w[(size_t)r * s->in[l] + c] = (float)((2 * uni() - 1) * lim);
+        std::vector<__nv_bfloat16> w16(nw);
+        for (size_t i = 0; i < nw; i++) w16[i] = __float2bfloat16_rn(w[i]);
+        cudaError_t e = cudaSuccess;
+        float **f[] = {&s->W[l], &s->gW[l], &s->mW[l], &s->vW[l]};
+        for (auto p : f)
+            if (e == cudaSuccess && (e = cudaMalloc(p, nw * 4)) == cudaSuccess) e = cudaMemset(*p, 0, nw * 4);
+        float **g[] = {&s->b[l], &s->gb[l], &s->mb[l], &s->vb[l]};
+        for (auto p : g)
+            if (e == cudaSuccess && (e = cudaMalloc(p, nb * 4)) == cudaSuccess) e = cudaMemset(*p, 0, nb * 4);
+        if (e == cudaSuccess) e = cudaMalloc(&s->W16[l], nw * 2);
+        if (e == cudaSuccess) e = cudaMemcpy(s->W[l], w.data(), nw * 4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(s->W16[l], w16.data(), nw * 2, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMalloc(&s->Z[l], (size_t)bmax * s->outp[l] * 4);
+        if (e == cudaSuccess) e = cudaMalloc(&s->dZ[l], (size_t)bmax * s->outp[l] * 2);
+        if (e == cudaSuccess) e = cudaMalloc(&s->A[l + 1], (size_t)bmax * s->outp[l] * 2);
+        if (e != cudaSuccess) rc = sur_fail(e);
+    }
+    if (rc == MG_OK) {
+        cudaError_t e = cudaMalloc(&s->A[0], (size_t)bmax * nin * 2);
+        if (e == cudaSuccess) e = cudaMalloc(&s->ms, 2 * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&s->part, (size_t)(bmax / 256 + 1) * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&s->y, (size_t)bmax * sizeof(float));
+        const double ms0[2] = {0.0, 1.0};
+        if (e == cudaSuccess) e = cudaMemcpy(s->ms, ms0, sizeof(ms0), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) rc = sur_fail(e);
+    }
+    if (rc != MG_OK) {
+        free_sur(s);
+        return rc;
+    }
+    *out = s;
+    return MG_OK;
+}
+
+void mg_sur_destroy(mg_surrogate *s) { free_sur(s); }
+
+// parameters as FP32 [W_0 (out x in), b_0 (out), W_1, b_1, ...] (unpadded)
+int mg_sur_param_count(const mg_surrogate *s, int64_t *n) {
+    if (!s || !n) return MG_ERR_BAD_ARG;
+    int64_t c = 0;
+    for (int l = 0; l < s->nl; l++) c += (int64_t)s->out[l] * s->in[l] + s->out[l];
+    *n = c;
+    return MG_OK;
+}
+
+static int copy_params(mg_surrogate *s, float *host, int to_host, int grads) {
+    size_t off = 0;
+    for (int l = 0; l < s->nl; l++) {
+        const size_t nw = (size_t)s->out[l] * s->in[l];
+        float *W = grads ? s->gW[l] : s->W[l];
+        float *b = grads ? s->gb[l] : s->b[l];
+        cudaError_t e;
+        if (to_host) {
+            e = cudaMemcpy(host + off, W, nw * 4, cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess) e = cudaMemcpy(host + off + nw, b, s->out[l] * 4, cudaMemcpyDeviceToHost);
+        } else {
+            e = cudaMemcpy(W, host + off, nw * 4, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemcpy(b, host + off + nw, s->out[l] * 4, cudaMemcpyHostToDevice);
+            std::vector<__nv_bfloat16> w16((size_t)s->outp[l] * s->in[l], __float2bfloat16_rn(0.0f));
+            for (size_t i = 0; i < nw; i++) w16[i] = __float2bfloat16_rn(host[off + i]);
+            if (e == cudaSuccess) e = cudaMemcpy(s->W16[l], w16.data(), w16.size() * 2, cudaMemcpyHostToDevice);
+        }
+        if (e != cudaSuccess) return sur_fail(e);
+        off += nw + s->out[l];
+    }
+    return MG_OK;
+}
+
+int mg_sur_get_params(mg_surrogate *s, float *host) {
+    if (!s || !host) return MG_ERR_BAD_ARG;
+    return copy_params(s, host, 1, 0);
+}
+int mg_sur_set_params(mg_surrogate *s, const float *host) {
+    if (!s || !host) return MG_ERR_BAD_ARG;
+    return copy_params(s, const_cast<float *>(host), 0, 0);
+}
+int mg_sur_get_grads(mg_surrogate *s, float *host) {
+    if (!s || !host) return MG_ERR_BAD_ARG;
+    return copy_params(s, host, 1, 1);
+}
+
+// mu, sigma of log|M|^2 over me_dev[n]
+int mg_sur_fit_target(mg_surrogate *s, const double *me, int64_t n, void *stream) {
+    if (!s || !me || n < 2) return MG_ERR_BAD_ARG;
+    k_logstats<<<1, 256, 0, (cudaStream_t)stream>>>(me, n, s->ms);
+    SCHECK(cudaGetLastError());
+    return MG_OK;
+}
+
+int mg_sur_get_target_stats(mg_surrogate *s, double *mu_sigma) {
+    if (!s || !mu_sigma) return MG_ERR_BAD_ARG;
+    SCHECK(cudaMemcpy(mu_sigma, s->ms, 2 * sizeof(double), cudaMemcpyDeviceToHost));
+    return MG_OK;
+}
+
+// Loss and gradients for one batch (rows of momenta [m][npar][4] with
+// targets y_dev[m] = standardised log|M|^2, FP32); m multiple of 16, <= bmax.
+int mg_sur_loss_grad(mg_surrogate *s, const double *mom, int npar, const float *y, int m,
+                     double *loss_out, void *stream) {
+    if (!s || !mom || !y || m < 16 || m % 16 || m > s->bmax || npar < 2) return MG_ERR_BAD_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    k_features<<<blocks_for(m, 128), 128, 0, st>>>(mom, m, npar, s->in[0], s->A[0]);
+    int rc = forward(s, m, st);
+    if (rc) return rc;
+    const int nb = blocks_for(m, 256);
+    k_loss<<<nb, 256, 0, st>>>(s->Z[s->nl - 1], m, s->outp[s->nl - 1], y, s->dZ[s->nl - 1], s->part);
+    rc = backward(s, m, st);
+    if (rc) return rc;
+    if (loss_out) {
+        std::vector<double> h(nb);
+        SCHECK(cudaMemcpyAsync(h.data(), s->part, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+        SCHECK(cudaStreamSynchronize(st));
+        double t = 0.0;
+        for (double v : h) t += v;
+        *loss_out = t / m;
+    }
+    return MG_OK;
+}
+
+int mg_sur_adam(mg_surrogate *s, double lr, void *stream) {
+    if (!s || !(lr > 0)) return MG_ERR_BAD_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    s->t++;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.0f - powf(b1, (float)s->t), c2 = 1.0f - powf(b2, (float)s->t);
+    for (int l = 0; l < s->nl; l++) {
+        const long long nw = (long long)s->outp[l] * s->in[l];
+        k_adam<<<blocks_for(nw, 256), 256, 0, st>>>(s->W[l], s->mW[l], s->vW[l], s->gW[l], s->W16[l], nw,
+                                                   (float)lr, b1, b2, 1e-8f, c1, c2);
+        k_adam<<<blocks_for(s->outp[l], 256), 256, 0, st>>>(s->b[l], s->mb[l], s->vb[l], s->gb[l], nullptr,
+                                                           s->outp[l], (float)lr, b1, b2, 1e-8f, c1, c2);
+    }
+    SCHECK(cudaGetLastError());
+    return MG_OK;
+}
+
+// Training: targets from me_dev (standardised with mg_sur_fit_target's mu,
+// sigma), full batches in data order, `epochs` passes, Adam after each batch.
+int mg_sur_train(mg_surrogate *s, const double *mom, int npar, const double *me, int64_t n,
+                 int epochs, int batch, double lr, void *stream, double *last_epoch_loss) {
+    if (!s || !mom || !me || batch < 16 || batch % 16 || batch > s->bmax || n < batch || epochs < 1)
+        return MG_ERR_BAD_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t nbatch = n / batch;
+    double acc = 0.0;
+    for (int ep = 0; ep < epochs; ep++) {
+        acc = 0.0;
+        for (int64_t bi = 0; bi < nbatch; bi++) {
+            const double *mb = mom + (size_t)bi * batch * npar * 4;
+            k_target<<<blocks_for(batch, 256), 256, 0, st>>>(me + bi * batch, batch, s->ms, s->y);
+            double l = 0.0;
+            int rc = mg_sur_loss_grad(s, mb, npar, s->y, batch, ep == epochs - 1 ? &l : nullptr, st);
+            if (rc) return rc;
+            acc += l;
+            rc = mg_sur_adam(s, lr, st);
+            if (rc) return rc;
+        }
+    }
+    if (last_epoch_loss) *last_epoch_loss = acc / (double)nbatch;
+    return MG_OK;
+}
+
+// Prediction of log|M|^2 for n events (chunks of bmax rows; n arbitrary).
+int mg_sur_predict(mg_surrogate *s, const double *mom, int npar, int64_t n, double *logme,
+                   void *stream) {
+    if (!s || !mom || !logme || n < 0) return MG_ERR_BAD_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int64_t e0 = 0; e0 < n; e0 += s->bmax) {
+        const int64_t c = (n - e0 < s->bmax) ? n - e0 : s->bmax;
+        const int M = (int)((c + WM - 1) / WM * WM);
+        k_features<<<blocks_for(c, 128), 128, 0, st>>>(mom + e0 * npar * 4, c, npar, s->in[0], s->A[0]);
+        if (M > c)
+            SCHECK(cudaMemsetAsync(s->A[0] + c * s->in[0], 0, (size_t)(M - c) * s->in[0] * 2, st));
+        int rc = forward(s, M, st);
+        if (rc) return rc;
+        k_pred<<<blocks_for(c, 256), 256, 0, st>>>(s->Z[s->nl - 1], s->outp[s->nl - 1], c, s->ms, logme + e0);
+    }
+    SCHECK(cudaGetLastError());
+    return MG_OK;
+}
+
+// Checkpoint: "MGSUR001", layer sizes, Adam step, mu/sigma, then per layer
+// W, b, m_W, v_W, m_b, v_b (FP32, padded shapes).
+int mg_sur_save(mg_surrogate *s, const char *path) {
+    if (!s || !path) return MG_ERR_BAD_ARG;
+    FILE *f = fopen(path, "wb");
+    if (!f) return MG_ERR_BAD_ARG;
+    int rc = MG_OK;
+    double ms[2];
+    int32_t hdr[2 + 2 * SUR_MAXL] = {s->nl, s->t};
+    for (int l = 0; l < s->nl; l++) {
+        hdr[2 + 2 * l] = s->in[l];
+        hdr[3 + 2 * l] = s->out[l];
+    }
+    if (cudaMemcpy(ms, s->ms, sizeof(ms), cudaMemcpyDeviceToHost) != cudaSuccess) rc = MG_ERR_CUDA;
+    if (!rc && (fwrite("MGSUR001", 1, 8, f) != 8 || fwrite(hdr, sizeof(hdr), 1, f) != 1 ||
+                fwrite(ms, sizeof(ms), 1, f) != 1))
+        rc = MG_ERR_BAD_ARG;
+    for (int l = 0; l < s->nl && !rc; l++) {
+        const size_t nw = (size_t)s->outp[l] * s->in[l], nb = s->outp[l];
+        float *arr[] = {s->W[l], s->b[l], s->mW[l], s->vW[l], s->mb[l], s->vb[l]};
+        size_t len[] = {nw, nb, nw, nw, nb, nb};
+        for (int k = 0; k < 6 && !rc; k++) {
+            std::vector<float> h(len[k]);
+            if (cudaMemcpy(h.data(), arr[k], len[k] * 4, cudaMemcpyDeviceToHost) != cudaSuccess) rc = MG_ERR_CUDA;
+            else if (fwrite(h.data(), 4, len[k], f) != len[k]) rc = MG_ERR_BAD_ARG;
+        }
+    }
+    fclose(f);
+    return rc;
+}
+
+int mg_sur_load(mg_surrogate *s, const char *path) {
+    if (!s || !path) return MG_ERR_BAD_ARG;
+    FILE *f = fopen(path, "rb");
+    if (!f) return MG_ERR_BAD_ARG;
+    char magic[8];
+    int32_t hdr[2 + 2 * SUR_MAXL];
+    double ms[2];
+    int rc = MG_OK;
+    if (fread(magic, 1, 8, f) != 8 || memcmp(magic, "MGSUR001", 8) || fread(hdr, sizeof(hdr), 1, f) != 1 ||
+        fread(ms, sizeof(ms), 1, f) != 1 || hdr[0] != s->nl)
+        rc = MG_ERR_BAD_ARG;
+    for (int l = 0; l < s->nl && !rc; l++)
+        if (hdr[2 + 2 * l] != s->in[l] || hdr[3 + 2 * l] != s->out[l]) rc = MG_ERR_BAD_ARG;
+    for (int l = 0; l < s->nl && !rc; l++) {
+        const size_t nw = (size_t)s->outp[l] * s->in[l], nb = s->outp[l];
+        float *arr[] = {s->W[l], s->b[l], s->mW[l], s->vW[l], s->mb[l], s->vb[l]};
+        size_t len[] = {nw, nb, nw, nw, nb, nb};
+        for (int k = 0; k < 6 && !rc; k++) {
+            std::vector<float> h(len[k]);
+            if (fread(h.data(), 4, len[k], f) != len[k]) rc = MG_ERR_BAD_ARG;
+            else if (cudaMemcpy(arr[k], h.data(), len[k] * 4, cudaMemcpyHostToDevice) != cudaSuccess) rc = MG_ERR_CUDA;
+            if (!rc && k == 0) {
+                std::vector<__nv_bfloat16> w16(nw);
+                for (size_t i = 0; i < nw; i++) w16[i] = __float2bfloat16_rn(h[i]);
+                if (cudaMemcpy(s->W16[l], w16.data(), nw * 2, cudaMemcpyHostToDevice) != cudaSuccess) rc = MG_ERR_CUDA;
+            }
+        }
+    }
+    if (!rc) {
+        s->t = hdr[1];
+        if (cudaMemcpy(s->ms, ms, sizeof(ms), cudaMemcpyHostToDevice) != cudaSuccess) rc = MG_ERR_CUDA;
+    }
+    fclose(f);
+    return rc;
+}
+
+// Two-stage unweighting of n candidates (see the file header).  Inputs on
+// the device: momenta [n][npar][4], phase-space weights phi[n], uniforms
+// u1[n], u2[n].  Outputs (device): accept[n] (0/1), weight[n] (0 if
+// rejected); *n_exact = candidates whose exact matrix element was computed.
+// Workspace (what[n], flags, indices, gathered momenta and exact matrix
+// elements of the stage-1 survivors) is allocated per call.
+int mg_unweight2(mg_process *p, mg_surrogate *s, const double *mom, const double *phi,
+                 const double *u1, const double *u2, int64_t n, double what_max, double r_max,
+                 unsigned char *accept, double *weight, int64_t *n_exact, void *stream) {
+    if (!p || !s || !mom || !phi || !u1 || !u2 || !accept || !weight || n < 1 || !(what_max > 0) ||
+        !(r_max > 0))
+        return MG_ERR_BAD_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int npar = p->tab->npar;
+    const int nb = blocks_for(n, 1024);
+    double *logme = nullptr, *what = nullptr, *mom1 = nullptr, *me1 = nullptr;
+    unsigned char *flag = nullptr;
+    int *bcount = nullptr;
+    long long *idx = nullptr, *total = nullptr, htotal = 0;
+    int rc = MG_OK;
+    cudaError_t e = cudaMalloc(&logme, n * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&what, n * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&flag, n);
+    if (e == cudaSuccess) e = cudaMalloc(&bcount, nb * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&total, sizeof(long long));
+    if (e == cudaSuccess) e = cudaMalloc(&idx, n * sizeof(long long));
+    if (e != cudaSuccess) rc = sur_fail(e);
+    if (!rc) rc = mg_sur_predict(s, mom, npar, n, logme, st);
+    if (!rc) {
+        k_stage1<<<nb, 1024, 0, st>>>(logme, phi, u1, n, what_max, what, flag, bcount);
+        k_scan<<<1, 32, 0, st>>>(bcount, nb, total);
+        e = cudaMemcpyAsync(&htotal, total, sizeof(long long), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = sur_fail(e);
+    }
+    if (!rc && htotal > 0) {
+        e = cudaMalloc(&mom1, htotal * npar * 4 * 8);
+        if (e == cudaSuccess) e = cudaMalloc(&me1, htotal * 8);
+        if (e != cudaSuccess) rc = sur_fail(e);
+        if (!rc) {
+            k_compact<<<nb, 1024, 0, st>>>(flag, bcount, n, mom, npar, idx, mom1);
+            rc = mg_sigmakin(p, mom1, htotal, me1, st);
+        }
+    }
+    if (!rc) {
+        e = cudaMemsetAsync(accept, 0, n, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(weight, 0, n * 8, st);
+        if (e != cudaSuccess) rc = sur_fail(e);
+        if (!rc && htotal > 0)
+            k_stage2<<<blocks_for(htotal, 256), 256, 0, st>>>(idx, me1, htotal, phi, what, u2, what_max,
+                                                             r_max, accept, weight);
+        e = cudaStreamSynchronize(st);
+        if (!rc && e != cudaSuccess) rc = sur_fail(e);
+    }
+    cudaFree(logme); cudaFree(what); cudaFree(flag); cudaFree(bcount); cudaFree(total);
+    cudaFree(idx); cudaFree(mom1); cudaFree(me1);
+    if (!rc && n_exact) *n_exact = htotal;
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,204 @@
+"""GPU: the MLP surrogate's own forward/backward kernels against the CPU
+oracle, its training, checkpointing, and the exact two-stage unweighting."""
+import ctypes
+import math
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import surrogate as S
+from paper_2510_05392_gb300 import binding
+from paper_2510_05392_gb300 import phasespace as ps
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SIZES = [32, 256, 256, 256, 1]
+
+
+def _lib():
+    L = binding.lib()
+    vp, dp, fp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float)
+    sig = {
+        "mg_sur_create": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
+                           ctypes.POINTER(vp)], ctypes.c_int),
+        "mg_sur_destroy": ([vp], None),
+        "mg_sur_param_count": ([vp, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+        "mg_sur_get_params": ([vp, fp], ctypes.c_int),
+        "mg_sur_set_params": ([vp, fp], ctypes.c_int),
+        "mg_sur_get_grads": ([vp, fp], ctypes.c_int),
+        "mg_sur_loss_grad": ([vp, vp, ctypes.c_int, vp, ctypes.c_int, dp, vp], ctypes.c_int),
+        "mg_sur_fit_target": ([vp, vp, ctypes.c_int64, vp], ctypes.c_int),
+        "mg_sur_get_target_stats": ([vp, dp], ctypes.c_int),
+        "mg_sur_train": ([vp, vp, ctypes.c_int, vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                          ctypes.c_double, vp, dp], ctypes.c_int),
+        "mg_sur_predict": ([vp, vp, ctypes.c_int, ctypes.c_int64, vp, vp], ctypes.c_int),
+        "mg_sur_save": ([vp, ctypes.c_char_p], ctypes.c_int),
+        "mg_sur_load": ([vp, ctypes.c_char_p], ctypes.c_int),
+        "mg_unweight2": ([vp, vp, vp, vp, vp, vp, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                          vp, vp, ctypes.POINTER(ctypes.c_int64), vp], ctypes.c_int),
+    }
+    for k, (a, r) in sig.items():
+        getattr(L, k).argtypes = a
+        getattr(L, k).restype = r
+    return L
+
+
+def _new(L, bmax=4096, seed=3):
+    h = ctypes.c_void_p()
+    assert L.mg_sur_create(32, 256, 3, seed, bmax, ctypes.byref(h)) == 0
+    return h
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _flat_to_params(flat):
+    out, off = [], 0
+    for a, b in zip(SIZES[:-1], SIZES[1:]):
+        W = flat[off:off + a * b].reshape(b, a).astype(np.float64)
+        off += a * b
+        out.append([W, flat[off:off + b].astype(np.float64)])
+        off += b
+    return out
+
+
+def _bf16(a):
+    t = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(torch.bfloat16)
+    return t.to(torch.float64).numpy()
+
+
+def test_gradients_match_cpu_oracle():
+    L = _lib()
+    h = _new(L)
+    n = ctypes.c_int64()
+    L.mg_sur_param_count(h, ctypes.byref(n))
+    flat = np.zeros(n.value, dtype=np.float32)
+    L.mg_sur_get_params(h, flat.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+    m = 512
+    mom = ps.generate(m, 2, 1500.0, 77, ptmin=20.0, drmin=0.4)
+    y = np.random.default_rng(0).normal(size=m).astype(np.float32)
+    loss = ctypes.c_double()
+    md, yd = torch.from_numpy(mom).cuda(), torch.from_numpy(y).cuda()
+    assert L.mg_sur_loss_grad(h, ctypes.c_void_p(md.data_ptr()), 6, ctypes.c_void_p(yd.data_ptr()), m,
+                              ctypes.byref(loss), _stream()) == 0
+    g = np.zeros_like(flat)
+    L.mg_sur_get_grads(h, g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+    # oracle on the same (BF16-rounded) weights and features, FP64 arithmetic
+    params = _flat_to_params(flat)
+    for p in params:
+        p[0] = _bf16(p[0])
+    x = _bf16(S.features(mom))
+    lo, go = S.loss_and_grads(params, x, y.astype(np.float64))
+    assert abs(loss.value / lo - 1) < 2e-2
+    gg = _flat_to_params(g)
+    for l in range(4):
+        for k in range(2):
+            ref = go[l][k]
+            err = np.linalg.norm(gg[l][k] - ref) / max(np.linalg.norm(ref), 1e-30)
+            assert err < 2e-2, (l, k, err)
+    L.mg_sur_destroy(h)
+
+
+def _train_set(ng, n, seed, sqrts=1500.0):
+    mom = ps.generate(n, ng, sqrts, seed, ptmin=20.0, drmin=0.4)
+    p = binding.Process("g g > t t~" + " g" * ng)
+    p.filter_helicities(torch.from_numpy(ps.generate(16, ng, sqrts, 12345, ptmin=20.0, drmin=0.4)).cuda())
+    md = torch.from_numpy(mom).cuda()
+    me = torch.empty(n, dtype=torch.float64, device="cuda")
+    p.sigmakin(md, me)
+    return p, mom, md, me
+
+
+def test_training_learns_log_me_and_checkpoint_roundtrip():
+    L = _lib()
+    p, mom, md, me = _train_set(2, 32768, 91)
+    h = _new(L)
+    s = _stream()
+    assert L.mg_sur_fit_target(h, ctypes.c_void_p(me.data_ptr()), 32768, s) == 0
+    first = ctypes.c_double()
+    assert L.mg_sur_train(h, ctypes.c_void_p(md.data_ptr()), 6, ctypes.c_void_p(me.data_ptr()), 32768,
+                          1, 4096, 1e-3, s, ctypes.byref(first)) == 0
+    last = ctypes.c_double()
+    assert L.mg_sur_train(h, ctypes.c_void_p(md.data_ptr()), 6, ctypes.c_void_p(me.data_ptr()), 32768,
+                          30, 4096, 1e-3, s, ctypes.byref(last)) == 0
+    assert last.value < 0.5 * first.value and last.value < 0.5   # standardised: 1 = no skill
+    # held-out events: prediction explains most of the variance of log|M|^2
+    _, mt, mtd, met = _train_set(2, 4096, 92)
+    pred = torch.empty(4096, dtype=torch.float64, device="cuda")
+    assert L.mg_sur_predict(h, ctypes.c_void_p(mtd.data_ptr()), 6, 4096, ctypes.c_void_p(pred.data_ptr()), s) == 0
+    torch.cuda.synchronize()
+    lt = torch.log(met)
+    r2 = 1 - ((pred - lt) ** 2).mean() / lt.var()
+    assert r2.item() > 0.5
+    with tempfile.TemporaryDirectory() as d:
+        f = os.path.join(d, "sur.bin").encode()
+        assert L.mg_sur_save(h, f) == 0
+        h2 = _new(L, seed=99)
+        assert L.mg_sur_load(h2, f) == 0
+        pred2 = torch.empty_like(pred)
+        L.mg_sur_predict(h2, ctypes.c_void_p(mtd.data_ptr()), 6, 4096, ctypes.c_void_p(pred2.data_ptr()), s)
+        torch.cuda.synchronize()
+        assert torch.equal(pred, pred2)
+        L.mg_sur_destroy(h2)
+    L.mg_sur_destroy(h)
+
+
+def test_two_stage_unweighting_exact_and_gain():
+    """Accept decisions match the oracle's rule on the same uniforms, and the
+    trained surrogate needs far fewer exact matrix elements per unweighted
+    event than plain hit-or-miss unweighting (exact matrix element on every
+    candidate)."""
+    L = _lib()
+    ng = 1
+    p, mom, md, me = _train_set(ng, 16384, 93)
+    h = _new(L)
+    s = _stream()
+    L.mg_sur_fit_target(h, ctypes.c_void_p(me.data_ptr()), 16384, s)
+    L.mg_sur_train(h, ctypes.c_void_p(md.data_ptr()), 5, ctypes.c_void_p(me.data_ptr()), 16384, 40, 4096,
+                   1e-3, s, None)
+    n = 65536
+    cand, phi, _ = ps.generate(n, ng, 1500.0, 94, ptmin=20.0, drmin=0.4, return_weights=True)
+    rng = np.random.default_rng(5)
+    u1, u2 = rng.uniform(size=n), rng.uniform(size=n)
+    cd = torch.from_numpy(cand).cuda()
+    pd, u1d, u2d = (torch.from_numpy(a).cuda() for a in (phi, u1, u2))
+    # calibration: maxima from the training slice (quantiles against outliers)
+    pred_tr = torch.empty(16384, dtype=torch.float64, device="cuda")
+    L.mg_sur_predict(h, ctypes.c_void_p(md.data_ptr()), 5, 16384, ctypes.c_void_p(pred_tr.data_ptr()), s)
+    _, phi_tr, _ = ps.generate(16384, ng, 1500.0, 93, ptmin=20.0, drmin=0.4, return_weights=True)
+    what_tr = np.exp(pred_tr.cpu().numpy()) * phi_tr
+    w_tr = me.cpu().numpy() * phi_tr
+    what_max = float(np.quantile(what_tr, 0.999))
+    r_max = float(np.quantile(w_tr / what_tr, 0.999))
+    acc = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    wt = torch.zeros(n, dtype=torch.float64, device="cuda")
+    nex = ctypes.c_int64()
+    assert L.mg_unweight2(p.handle, h, ctypes.c_void_p(cd.data_ptr()), ctypes.c_void_p(pd.data_ptr()),
+                          ctypes.c_void_p(u1d.data_ptr()), ctypes.c_void_p(u2d.data_ptr()), n, what_max,
+                          r_max, ctypes.c_void_p(acc.data_ptr()), ctypes.c_void_p(wt.data_ptr()),
+                          ctypes.byref(nex), s) == 0
+    acc_g, wt_g = acc.cpu().numpy().astype(bool), wt.cpu().numpy()
+    # oracle rule with the oracle's exact |M|^2 and the GPU surrogate's w_hat
+    pred = torch.empty(n, dtype=torch.float64, device="cuda")
+    L.mg_sur_predict(h, ctypes.c_void_p(cd.data_ptr()), 5, n, ctypes.c_void_p(pred.data_ptr()), s)
+    what = np.exp(pred.cpu().numpy()) * phi
+    s1 = u1 < what / what_max
+    w = np.zeros(n)
+    w[s1] = oracle.me(cand[s1]) * phi[s1]
+    acc_o, wt_o, s1_o = S.unweight_two_stage(w, what, u1, u2, what_max, r_max)
+    assert nex.value == int(s1_o.sum())
+    near = np.abs((w / what) / r_max - u2) < 1e-8
+    assert np.array_equal(acc_g[~near], acc_o[~near])
+    np.testing.assert_allclose(wt_g[acc_g & acc_o], wt_o[acc_g & acc_o], rtol=1e-9)
+    # gain: exact evaluations per unweighted event, two-stage vs plain
+    w_all = w_tr.max()
+    plain_evals_per_event = w_all / w_tr.mean()
+    two_stage_evals_per_event = nex.value / max(1, acc_g.sum())
+    print(f"exact MEs per unweighted event: plain {plain_evals_per_event:.1f}, "
+          f"two-stage {two_stage_evals_per_event:.1f}")
+    assert two_stage_evals_per_event < plain_evals_per_event / 2

@@ -60,20 +60,41 @@ def init_params(sizes, seed=0):
     return ps
 
 
-def forward(params, x):
-    """Returns (f, cache) with cache = [(a_prev, z)] per layer."""
+def round_bf16(a):
+    """Round to bfloat16 (8 significant bits), round-to-nearest-even, via the
+    float32 bit pattern: keep the high 16 bits after adding 0x7FFF plus the
+    lowest kept bit.  Returns float64."""
+    f = np.ascontiguousarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward(params, x, emulate_bf16=False):
+    """Returns (f, cache) with cache = [(a_prev, z)] per layer.  With
+    emulate_bf16 the hidden activations are rounded to bfloat16 where the
+    BF16 training stores them (the arithmetic stays FP64)."""
     a = x
     cache = []
     for l, (W, b) in enumerate(params):
         z = a @ W.T + b
         cache.append((a, z))
-        a = silu(z) if l + 1 < len(params) else z
+        if l + 1 < len(params):
+            a = silu(z)
+            if emulate_bf16:
+                a = round_bf16(a)
+        else:
+            a = z
     return a[:, 0], cache
 
 
-def loss_and_grads(params, x, y):
-    """Mean-squared error and its gradients (hand-derived chain rule)."""
-    f, cache = forward(params, x)
+def loss_and_grads(params, x, y, emulate_bf16=False):
+    """Mean-squared error and its gradients (hand-derived chain rule).
+
+    emulate_bf16: the backward operands of the BF16 training are rounded to
+    bfloat16 where it rounds them (the output gradient dz of each layer before
+    it multiplies weights or activations); bias gradients sum the unrounded dz."""
+    f, cache = forward(params, x, emulate_bf16)
     n = len(y)
     loss = float(np.mean((f - y) ** 2))
     dz = (2.0 / n) * (f - y)[:, None]
@@ -83,8 +104,9 @@ def loss_and_grads(params, x, y):
         if l + 1 < len(params):
             dz = dz * dsilu(z)
         W, _ = params[l]
-        grads[l] = [dz.T @ a_prev, dz.sum(0)]
-        dz = dz @ W
+        dzq = round_bf16(dz) if emulate_bf16 else dz
+        grads[l] = [dzq.T @ a_prev, dz.sum(0)]
+        dz = dzq @ W
     return loss, grads
 
 

@@ -95,7 +95,7 @@ __global__ void k_fwd(const __nv_bfloat16 *__restrict__ A, const __nv_bfloat16 *
 // silu'(Zprev).  One warp per 16x16 tile.
 __global__ void k_bwd_data(const __nv_bfloat16 *__restrict__ dZ, const __nv_bfloat16 *__restrict__ W,
                            const float *__restrict__ Zprev, int M, int N, int K,
-                           __nv_bfloat16 *__restrict__ dZprev) {
+                           __nv_bfloat16 *__restrict__ dZprev, float *__restrict__ dZprev32) {
     __shared__ float tile[4][WM * WM];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int t = blockIdx.x * 4 + warp;
@@ -116,7 +116,9 @@ __global__ void k_bwd_data(const __nv_bfloat16 *__restrict__ dZ, const __nv_bflo
     for (int q = lane; q < WM * WM; q += 32) {
         const int r = q / WM, cc = q % WM;
         const long long o = (long long)(m0 + r) * K + k0 + cc;
-        dZprev[o] = __float2bfloat16_rn(tile[warp][q] * dsilu_f(Zprev[o]));
+        const float d = tile[warp][q] * dsilu_f(Zprev[o]);
+        dZprev[o] = __float2bfloat16_rn(d);
+        dZprev32[o] = d;
     }
 }
 
@@ -140,19 +142,21 @@ __global__ void k_bwd_weight(const __nv_bfloat16 *__restrict__ dZ, const __nv_bf
     wmma::store_matrix_sync(gW + (long long)n0 * K + k0, c, K, wmma::mem_row_major);
 }
 
-// gb[n] = sum_m dZ[m][n]
-__global__ void k_bias_grad(const __nv_bfloat16 *__restrict__ dZ, int M, int N, float *__restrict__ gb) {
+// gb[n] = sum_m dZ[m][n] from the FP32 values (the BF16 copies feed the
+// weight-gradient GEMM; their rounding would not cancel in this sum)
+__global__ void k_bias_grad(const float *__restrict__ dZ, int M, int N, float *__restrict__ gb) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
-    float s = 0.0f;
-    for (int m = 0; m < M; m++) s += __bfloat162float(dZ[(long long)m * N + n]);
-    gb[n] = s;
+    double s = 0.0;
+    for (int m = 0; m < M; m++) s += dZ[(long long)m * N + n];
+    gb[n] = (float)s;
 }
 
 // Output-layer loss gradient: dZ[m][0] = 2 (f_m - y_m) / M (other padded
 // columns 0); per-block partial sums of the squared error.
 __global__ void k_loss(const float *__restrict__ Zout, int M, int N, const float *__restrict__ y,
-                       __nv_bfloat16 *__restrict__ dZ, double *__restrict__ part) {
+                       __nv_bfloat16 *__restrict__ dZ, float *__restrict__ dZ32,
+                       double *__restrict__ part) {
     __shared__ double red[256];
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     double se = 0.0;
@@ -160,7 +164,11 @@ __global__ void k_loss(const float *__restrict__ Zout, int M, int N, const float
         const float d = Zout[(long long)m * N] - y[m];
         se = (double)d * d;
         dZ[(long long)m * N] = __float2bfloat16_rn(2.0f * d / M);
-        for (int c = 1; c < N; c++) dZ[(long long)m * N + c] = __float2bfloat16_rn(0.0f);
+        dZ32[(long long)m * N] = 2.0f * d / M;
+        for (int c = 1; c < N; c++) {
+            dZ[(long long)m * N + c] = __float2bfloat16_rn(0.0f);
+            dZ32[(long long)m * N + c] = 0.0f;
+        }
     }
     red[threadIdx.x] = se;
     __syncthreads();
@@ -315,6 +323,7 @@ struct mg_surrogate {
     __nv_bfloat16 *A[SUR_MAXL + 1];  // activations (A[0] = features)
     float *Z[SUR_MAXL];
     __nv_bfloat16 *dZ[SUR_MAXL];
+    float *dZ32[SUR_MAXL];
     double *ms;                  // mu, sigma of log|M|^2 (device)
     double *part;                // loss partial sums
     float *y;                    // standardised targets of a chunk
@@ -335,7 +344,7 @@ void free_sur(mg_surrogate *s) {
     for (int l = 0; l < SUR_MAXL; l++) {
         cudaFree(s->W[l]); cudaFree(s->b[l]); cudaFree(s->gW[l]); cudaFree(s->gb[l]);
         cudaFree(s->mW[l]); cudaFree(s->vW[l]); cudaFree(s->mb[l]); cudaFree(s->vb[l]);
-        cudaFree(s->W16[l]); cudaFree(s->Z[l]); cudaFree(s->dZ[l]);
+        cudaFree(s->W16[l]); cudaFree(s->Z[l]); cudaFree(s->dZ[l]); cudaFree(s->dZ32[l]);
     }
     for (int l = 0; l <= SUR_MAXL; l++) cudaFree(s->A[l]);
     cudaFree(s->ms); cudaFree(s->part); cudaFree(s->y);
@@ -363,11 +372,12 @@ int backward(mg_surrogate *s, int M, cudaStream_t st) {
         const int tiles_w = (s->outp[l] / WM) * (s->in[l] / WM);
         k_bwd_weight<<<blocks_for(tiles_w, 4), 128, 0, st>>>(s->dZ[l], s->A[l], M, s->outp[l],
                                                             s->in[l], s->gW[l]);
-        k_bias_grad<<<blocks_for(s->outp[l], 128), 128, 0, st>>>(s->dZ[l], M, s->outp[l], s->gb[l]);
+        k_bias_grad<<<blocks_for(s->outp[l], 128), 128, 0, st>>>(s->dZ32[l], M, s->outp[l], s->gb[l]);
         if (l > 0) {
             const int tiles_d = (M / WM) * (s->in[l] / WM);
             k_bwd_data<<<blocks_for(tiles_d, 4), 128, 0, st>>>(s->dZ[l], s->W16[l], s->Z[l - 1], M,
-                                                              s->outp[l], s->in[l], s->dZ[l - 1]);
+                                                              s->outp[l], s->in[l], s->dZ[l - 1],
+                                                              s->dZ32[l - 1]);
         }
     }
     SCHECK(cudaGetLastError());
@@ -419,6 +429,7 @@ int mg_sur_create(int nin, int hidden, int nhidden, uint64_t seed, int bmax, mg_
         if (e == cudaSuccess) e = cudaMemcpy(s->W16[l], w16.data(), nw * 2, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMalloc(&s->Z[l], (size_t)bmax * s->outp[l] * 4);
         if (e == cudaSuccess) e = cudaMalloc(&s->dZ[l], (size_t)bmax * s->outp[l] * 2);
+        if (e == cudaSuccess) e = cudaMalloc(&s->dZ32[l], (size_t)bmax * s->outp[l] * 4);
         if (e == cudaSuccess) e = cudaMalloc(&s->A[l + 1], (size_t)bmax * s->outp[l] * 2);
         if (e != cudaSuccess) rc = sur_fail(e);
     }
@@ -486,6 +497,28 @@ int mg_sur_get_grads(mg_surrogate *s, float *host) {
     return copy_params(s, host, 1, 1);
 }
 
+// Copies an internal buffer of the last forward/backward pass to the host
+// (FP32 out[rows][cols], padded widths): which = 0 activations A[layer]
+// (layer 0 = features), 1 pre-activations Z[layer], 2 gradients dZ[layer] (FP32).
+int mg_sur_debug_buffer(mg_surrogate *s, int which, int layer, int rows, float *out) {
+    if (!s || !out || rows < 1 || rows > s->bmax || layer < 0) return MG_ERR_BAD_ARG;
+    int cols = 0;
+    if (which == 0 && layer <= s->nl - 1) {
+        cols = layer == 0 ? s->in[0] : s->outp[layer - 1];
+        std::vector<__nv_bfloat16> h((size_t)rows * cols);
+        SCHECK(cudaMemcpy(h.data(), s->A[layer], h.size() * 2, cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < h.size(); i++) out[i] = __bfloat162float(h[i]);
+        return MG_OK;
+    }
+    if ((which == 1 || which == 2) && layer < s->nl) {
+        cols = s->outp[layer];
+        SCHECK(cudaMemcpy(out, which == 1 ? s->Z[layer] : s->dZ32[layer], (size_t)rows * cols * 4,
+                          cudaMemcpyDeviceToHost));
+        return MG_OK;
+    }
+    return MG_ERR_BAD_ARG;
+}
+
 // mu, sigma of log|M|^2 over me_dev[n]
 int mg_sur_fit_target(mg_surrogate *s, const double *me, int64_t n, void *stream) {
     if (!s || !me || n < 2) return MG_ERR_BAD_ARG;
@@ -510,7 +543,8 @@ int mg_sur_loss_grad(mg_surrogate *s, const double *mom, int npar, const float *
     int rc = forward(s, m, st);
     if (rc) return rc;
     const int nb = blocks_for(m, 256);
-    k_loss<<<nb, 256, 0, st>>>(s->Z[s->nl - 1], m, s->outp[s->nl - 1], y, s->dZ[s->nl - 1], s->part);
+    k_loss<<<nb, 256, 0, st>>>(s->Z[s->nl - 1], m, s->outp[s->nl - 1], y, s->dZ[s->nl - 1],
+                               s->dZ32[s->nl - 1], s->part);
     rc = backward(s, m, st);
     if (rc) return rc;
     if (loss_out) {

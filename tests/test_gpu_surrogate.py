@@ -88,20 +88,30 @@ def test_gradients_match_cpu_oracle():
                               ctypes.byref(loss), _stream()) == 0
     g = np.zeros_like(flat)
     L.mg_sur_get_grads(h, g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
-    # oracle on the same (BF16-rounded) weights and features, FP64 arithmetic
+    # oracle on the same (BF16-rounded) weights and features, FP64 arithmetic,
+    # rounding to BF16 where the BF16 training stores values
     params = _flat_to_params(flat)
     for p in params:
-        p[0] = _bf16(p[0])
-    x = _bf16(S.features(mom))
-    lo, go = S.loss_and_grads(params, x, y.astype(np.float64))
-    assert abs(loss.value / lo - 1) < 2e-2
+        p[0] = S.round_bf16(p[0])
+    x = S.round_bf16(S.features(mom))
+    lo, go = S.loss_and_grads(params, x, y.astype(np.float64), emulate_bf16=True)
+    _, gx = S.loss_and_grads(params, x, y.astype(np.float64))
+    assert abs(loss.value / lo - 1) < 1e-5
     gg = _flat_to_params(g)
+    errs, errs_exact = {}, {}
     for l in range(4):
         for k in range(2):
-            ref = go[l][k]
-            err = np.linalg.norm(gg[l][k] - ref) / max(np.linalg.norm(ref), 1e-30)
-            assert err < 2e-2, (l, k, err)
+            nrm = lambda a, b: np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+            errs[(l, k)] = nrm(gg[l][k], go[l][k])
+            errs_exact[(l, k)] = nrm(gg[l][k], gx[l][k])
+    print("gradient errors vs BF16-emulating oracle:", errs)
+    print("gradient errors vs exact FP64 oracle:", errs_exact)
     L.mg_sur_destroy(h)
+    # residuals: values rounded to the other BF16 neighbour when FP32 and FP64
+    # accumulation straddle a rounding boundary; bias sums cancel the most
+    assert max(errs[(l, 0)] for l in range(4)) < 2e-3, errs
+    assert max(errs[(l, 1)] for l in range(4)) < 5e-3, errs
+    assert max(errs_exact[(l, 0)] for l in range(4)) < 3e-2
 
 
 def _train_set(ng, n, seed, sqrts=1500.0):

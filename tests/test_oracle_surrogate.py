@@ -80,3 +80,26 @@ def test_unweighting_special_cases_and_unbiasedness():
     acc, wt, s1 = S.unweight_two_stage(w, what, u1, u2, wmax, rmax)
     est = wt.sum() * wmax * rmax
     assert abs(est / w.sum() - 1) < 0.02
+
+
+def test_bf16_rounding_reference_values():
+    r = S.round_bf16
+    assert r(np.array([1.0]))[0] == 1.0
+    assert r(np.array([1.0 + 2.0 ** -9]))[0] == 1.0              # tie -> even
+    assert r(np.array([1.0 + 3 * 2.0 ** -9]))[0] == 1.0 + 2.0 ** -7
+    assert r(np.array([-3.0 - 2.0 ** -8]))[0] == -3.0
+    x = np.random.default_rng(0).normal(size=1000)
+    assert np.all(np.abs(r(x) / x - 1) <= 2.0 ** -8)
+    y = r(x)
+    np.testing.assert_array_equal(r(y), y)
+
+
+def test_emulated_bf16_gradients_close_to_exact():
+    rng = np.random.default_rng(2)
+    params = S.init_params([32, 64, 64, 1], seed=1)
+    x = rng.uniform(0, 1, (128, 32))
+    y = rng.normal(size=128)
+    _, g = S.loss_and_grads(params, x, y)
+    _, ge = S.loss_and_grads(params, x, y, emulate_bf16=True)
+    for l in range(3):
+        assert np.linalg.norm(ge[l][0] - g[l][0]) < 0.05 * np.linalg.norm(g[l][0])

@@ -235,6 +235,125 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def _sur_lib():
+    from paper_2510_05392_gb300 import binding
+    L = binding.lib()
+    vp, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "mg_sur_create": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
+                          ctypes.POINTER(vp)],
+        "mg_sur_fit_target": [vp, vp, ctypes.c_int64, vp],
+        "mg_sur_train": [vp, vp, ctypes.c_int, vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                         ctypes.c_double, vp, dp],
+        "mg_sur_predict": [vp, vp, ctypes.c_int, ctypes.c_int64, vp, vp],
+        "mg_unweight2": [vp, vp, vp, vp, vp, vp, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                         vp, vp, ctypes.POINTER(ctypes.c_int64), vp],
+        "mg_sur_destroy": [vp],
+    }
+    for k, a in sig.items():
+        getattr(L, k).argtypes = a
+    return L
+
+
+def run_surrogate(args):
+    """g g -> t t~ g g g g at sqrt(s) = 2000 GeV with cuts: exact FP64 matrix
+    elements of the training events, MLP training on the GPU, two-stage
+    unweighting of the candidates (exact FP64 matrix element only for the
+    stage-1 survivors), against plain hit-or-miss unweighting (exact matrix
+    element for every candidate, at the measured exact rate)."""
+    import numpy as np
+    import torch
+    from paper_2510_05392_gb300 import binding, build
+    from paper_2510_05392_gb300 import phasespace as ps
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    L = _sur_lib()
+    ntrain = args.nevt or 262144
+    ncand = args.ncand
+    sqrts, seed = 2000.0, 20251005 + 5
+    kw = dict(ptmin=20.0, drmin=0.4)
+    tr, phi_tr, _ = ps.generate(ntrain, 4, sqrts, seed, return_weights=True, **kw)
+    ca, phi_ca, _ = ps.generate(ncand, 4, sqrts, seed + 1000, return_weights=True, **kw)
+    rng = np.random.default_rng(seed)
+    u1, u2 = rng.uniform(size=ncand), rng.uniform(size=ncand)
+    p = binding.Process("g g > t t~ g g g g")
+    p.filter_helicities(torch.from_numpy(ps.generate(16, 4, sqrts, TEST_SEED, **kw)).to(dev))
+    p.set_launch(16, 128)
+    stream = torch.cuda.current_stream(dev)
+    sp = ctypes.c_void_p(stream.cuda_stream)
+    trd = torch.from_numpy(tr).to(dev)
+    me_tr = torch.empty(ntrain, dtype=torch.float64, device=dev)
+    p.sigmakin(trd[:256], me_tr[:256], stream)  # warm-up
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    p.sigmakin(trd, me_tr, stream)
+    torch.cuda.synchronize(dev)
+    t_exact = time.perf_counter() - t0
+    rate_exact = ntrain / t_exact
+    # surrogate training
+    h = ctypes.c_void_p()
+    assert L.mg_sur_create(32, 256, 3, 7, 4096, ctypes.byref(h)) == 0
+    t0 = time.perf_counter()
+    L.mg_sur_fit_target(h, ctypes.c_void_p(me_tr.data_ptr()), ntrain, sp)
+    loss = ctypes.c_double()
+    rc = L.mg_sur_train(h, ctypes.c_void_p(trd.data_ptr()), 8, ctypes.c_void_p(me_tr.data_ptr()), ntrain,
+                        args.epochs, 4096, 1e-3, sp, ctypes.byref(loss))
+    torch.cuda.synchronize(dev)
+    t_train = time.perf_counter() - t0
+    assert rc == 0, rc
+    # calibration on the training slice
+    pred_tr = torch.empty(ntrain, dtype=torch.float64, device=dev)
+    L.mg_sur_predict(h, ctypes.c_void_p(trd.data_ptr()), 8, ntrain, ctypes.c_void_p(pred_tr.data_ptr()), sp)
+    torch.cuda.synchronize(dev)
+    w_tr = me_tr.cpu().numpy() * phi_tr
+    what_tr = np.exp(pred_tr.cpu().numpy()) * phi_tr
+    what_max = float(np.quantile(what_tr, 0.999))
+    r_max = float(np.quantile(w_tr / what_tr, 0.999))
+    lt = np.log(me_tr.cpu().numpy())
+    r2 = 1 - np.mean((pred_tr.cpu().numpy() - lt) ** 2) / np.var(lt)
+    # two-stage unweighting of the candidates
+    cad = torch.from_numpy(ca).to(dev)
+    phd, u1d, u2d = (torch.from_numpy(a).to(dev) for a in (phi_ca, u1, u2))
+    acc = torch.zeros(ncand, dtype=torch.uint8, device=dev)
+    wt = torch.zeros(ncand, dtype=torch.float64, device=dev)
+    nex = ctypes.c_int64()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    rc = L.mg_unweight2(p.handle, h, ctypes.c_void_p(cad.data_ptr()), ctypes.c_void_p(phd.data_ptr()),
+                        ctypes.c_void_p(u1d.data_ptr()), ctypes.c_void_p(u2d.data_ptr()), ncand, what_max,
+                        r_max, ctypes.c_void_p(acc.data_ptr()), ctypes.c_void_p(wt.data_ptr()),
+                        ctypes.byref(nex), sp)
+    torch.cuda.synchronize(dev)
+    t_two = time.perf_counter() - t0
+    assert rc == 0, rc
+    wts = wt.cpu().numpy()
+    nacc = int((acc.cpu().numpy() != 0).sum())
+    kish = float(wts.sum() ** 2 / max((wts ** 2).sum(), 1e-300))
+    eff_plain = float(w_tr.mean() / w_tr.max())          # hit-or-miss with w_max of the same slice
+    plain_unw_per_s = rate_exact * eff_plain
+    two_unw_per_s = nacc / t_two
+    line = {
+        "metric": METRIC, "value": ncand / t_two, "unit": "events/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+        "ms_per_step": 1e3 * t_two, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 (exact ME) + bf16 (surrogate)", "data": "synthetic (Philox4x32-10 + massive RAMBO, gluon cuts)",
+        "config": {"workload": "ggttgggg_surrogate", "process": "g g > t t~ g g g g", "sqrt_s_gev": sqrts,
+                   "train_events": ntrain, "candidates": ncand, "epochs": args.epochs, "batch": 4096,
+                   "mlp": "32(28 s_ij/s)-256-256-256-1 SiLU, BF16 weights/activations, FP32 master + Adam"},
+        "exact_fp64": {"events_per_s": rate_exact, "seconds": t_exact,
+                       "fp64_tflops": rate_exact * p.info().ngood * (p.info().flops_diagram + p.info().flops_colour) / 1e12},
+        "training": {"seconds": t_train, "final_epoch_loss": loss.value, "r2_log_me_train": float(r2)},
+        "two_stage": {"seconds": t_two, "exact_evaluations": int(nex.value), "accepted": nacc,
+                      "what_max": what_max, "r_max": r_max, "kish_ess": kish,
+                      "unweighted_events_per_s": two_unw_per_s},
+        "plain_hit_or_miss": {"efficiency": eff_plain, "unweighted_events_per_s": plain_unw_per_s},
+        "surrogate_gain_unweighted_events_per_s": two_unw_per_s / plain_unw_per_s,
+        "gpu_launches": None,
+    }
+    print(json.dumps(line), flush=True)
+    L.mg_sur_destroy(h)
+
+
 def run_ours(args):
     import torch
     from paper_2510_05392_gb300 import binding, build
@@ -393,7 +512,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="ggttgg_524288",
-                    choices=sorted(WORKLOADS) + ["uneven_batch_4proc"])
+                    choices=sorted(WORKLOADS) + ["uneven_batch_4proc", "ggttgggg_surrogate"])
+    ap.add_argument("--ncand", type=int, default=1048576, help="surrogate: candidates")
+    ap.add_argument("--epochs", type=int, default=20, help="surrogate: training epochs")
     ap.add_argument("--nevt", type=int, default=0, help="override events per GPU (profiling)")
     ap.add_argument("--tpe", type=int, default=0)
     ap.add_argument("--block", type=int, default=0)
@@ -411,6 +532,8 @@ def main():
         run_reference(args)
     elif args.workload == "uneven_batch_4proc":
         run_batch(args)
+    elif args.workload == "ggttgggg_surrogate":
+        run_surrogate(args)
     else:
         run_ours(args)
 

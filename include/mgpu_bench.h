@@ -24,6 +24,13 @@ int mg_probe_fp64_peak(int blocks, int iters, int reps, double *flops_out);
 struct mg_process;
 int mg_debug_inject_stall(struct mg_process *p, unsigned int extra_bytes);
 
+/* Copies an internal buffer of the surrogate's last forward/backward pass to
+ * the host as FP32 out[rows][cols] (padded widths): which = 0 activations of
+ * layer input `layer` (0 = features), 1 pre-activations, 2 FP32 output
+ * gradients of layer `layer`. */
+struct mg_surrogate;
+int mg_sur_debug_buffer(struct mg_surrogate *s, int which, int layer, int rows, float *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -65,6 +65,10 @@ def algorithmic_flops(prog: program.Program) -> dict:
         sh, pv, nv = FLOPS[op[0]]
         unit += sh + pv * nv
     unit += JAMP_UPDATE_FLOPS * 4 * len(prog.scatter)
+    # amplitudes added into their colour group's accumulator (all but the first)
+    unit += JAMP_UPDATE_FLOPS * 4 * sum(
+        1 for op in prog.ops if op[0] in (program.OP_AMP_SS, program.OP_AMP_VV)
+        and op[6] >= 0 and not op[7] & 4)
     nc = prog.ncolor
     csum = 2 * (nc * (nc + 1) // 2) * 2 + 2 * nc
     return dict(diagram=unit / 4.0, colour=csum)
@@ -83,7 +87,8 @@ def _arr(name, vals, per_line=16):
 def emit(path: str, max_gluons: int = 6, list_path: str | None = None) -> None:
     """Write the table include file ``path`` and, next to it (or at
     ``list_path``), mg_proc_list.h with one X(index, ngluon, nslot_gluon,
-    nslot_top, ncolor) entry per process for the kernel instantiations."""
+    nslot_top, nslot_acc, ncolor) entry per process for the kernel
+    instantiations."""
     lines = ["/* generated by paper_2510_05392_gb300.compiler.emit -- do not edit */",
              "#pragma once", "#include <stdint.h>", ""]
     rows = []
@@ -104,10 +109,12 @@ def emit(path: str, max_gluons: int = 6, list_path: str | None = None) -> None:
         iden = 256 * math.factorial(n - 2)
         rows.append(
             f'  {{"{name}", "{proc}", {n}, {n + 2}, {prog.ndiagrams}, {prog.nterms}, '
-            f'{prog.ncolor}, {prog.nslot}, {prog.nslot_f}, {len(prog.ops)}, {len(prog.scatter)}, '
+            f'{prog.ncolor}, {prog.nslot}, {prog.nslot_f}, {prog.nslot_acc}, {len(prog.ops)}, '
+            f'{len(prog.scatter)}, '
             f'{D}LL, {iden}.0, {fl["diagram"]!r}, {fl["colour"]}.0, OPS_{name}, SCAT_{name}, '
             f'CHAT_{name}}},')
-        xlist.append(f"X({len(rows) - 1}, {n}, {prog.nslot}, {prog.nslot_f}, {prog.ncolor})")
+        xlist.append(f"X({len(rows) - 1}, {n}, {prog.nslot}, {prog.nslot_f}, {max(1, prog.nslot_acc)}, "
+                     f"{prog.ncolor})")
         lines.append("")
     lines.append("static const mg_proc_table MG_PROC_TABLES[] = {")
     lines.extend(rows)

@@ -37,8 +37,8 @@ OP_FSUF = 7     # out, V, J, set                 V' = (q+m) Jslash V dS[set]
 OP_XROW = 8     # out, U, J                      X = U Jslash
 OP_YCOL = 9     # out, J, V                      Y = Jslash V
 OP_BIL = 10     # out, U, V                      G^mu = U gamma^mu V
-OP_AMP_SS = 11  # X, V, scatter offset, count    amp = X . V
-OP_AMP_VV = 12  # G, J, scatter offset, count    amp = G . J (Minkowski)
+OP_AMP_SS = 11  # X, V, scatter offset, count, acc, mode   amp = X . V
+OP_AMP_VV = 12  # G, J, scatter offset, count, acc, mode   amp = G . J (Minkowski)
 
 OPNAMES = {v: k for k, v in dict(globals()).items() if k.startswith("OP_")}
 
@@ -58,6 +58,8 @@ class Program:
     scatter: list = field(default_factory=list)    # jamp*4 + coef
     nslot: int = 0                                 # gluon-wavefunction slots (1 variant)
     nslot_f: int = 0                               # top-line slots (2 variants)
+    nslot_acc: int = 0                             # amplitude accumulators (4 variants)
+    ncolour_groups: int = 0                        # distinct colour factors up to a phase
     ndiagrams: int = 0
     nterms: int = 0
     perms: list = field(default_factory=list)      # colour-flow orderings
@@ -236,8 +238,26 @@ def build_program(n: int, order: str = "middle") -> Program:
         return tuple((-len(c.gset), c.idx) for c in ds)
     terms.sort(key=sort_key)
 
+    # Diagram terms whose colour factors agree up to a unit phase share their
+    # scatter: their amplitudes are summed (with that phase) into an
+    # accumulator and the group's last member scatters the sum once.  (The
+    # number of such classes is the paper's count of single-diagram-enhancement
+    # channels: 3 / 15 / 105 / 945 for 2 to 5 gluons.)
+    group_of, phase_of, rep = {}, {}, {}
+    for d, _ in terms:
+        items = sorted(d.color.items(), key=lambda kv: pidx[kv[0]])
+        c0 = complex(items[0][1])
+        key = tuple((st, complex(c) / c0) for st, c in items)
+        if key not in rep:
+            rep[key] = (len(rep), items, c0)
+        group_of[d.idx] = rep[key][0]
+        phase_of[d.idx] = c0
+    members = {}
+    for d, _ in terms:
+        members.setdefault(group_of[d.idx], []).append(d.idx)
+    rep_items = {g: (it, c0) for _, (g, it, c0) in rep.items()}
+
     scatter = []
-    amp_ops = []
     for d, s in terms:
         if s is None:
             g = B.g0()
@@ -253,10 +273,27 @@ def build_program(n: int, order: str = "middle") -> Program:
                 u = B.prefix(L)
                 y = B.ycol(M, R)
                 code, ins = OP_AMP_SS, [u, y]
-        off = len(scatter)
-        for string, c in sorted(d.color.items(), key=lambda kv: pidx[kv[0]]):
-            scatter.append(pidx[string] * 4 + COEF_CODE[complex(c) if isinstance(c, complex) else c])
-        B._emit(code, [], ins, [off, len(scatter) - off])
+        g = group_of[d.idx]
+        mem = members[g]
+        if len(mem) == 1:
+            off = len(scatter)
+            for string, c in sorted(d.color.items(), key=lambda kv: pidx[kv[0]]):
+                scatter.append(pidx[string] * 4 + COEF_CODE[complex(c)])
+            B._emit(code, [], ins, [off, len(scatter) - off, None, 0])
+            continue
+        first, last = mem[0] == d.idx, mem[-1] == d.idx
+        acc_key = ("ACC", g)
+        outs = [B._new(acc_key)] if first else []
+        acc_in = [] if first else [B.obj[acc_key]]
+        off = cnt = 0
+        if last:
+            items, c0 = rep_items[g]
+            off = len(scatter)
+            for string, c in items:
+                scatter.append(pidx[string] * 4 + COEF_CODE[complex(c) / c0])
+            cnt = len(scatter) - off
+        mode = COEF_CODE[phase_of[d.idx]] | (4 if first else 0) | (8 if last else 0)
+        B._emit(code, outs, ins + acc_in, [off, cnt, "acc", mode])
 
     # ------------------------------------------------ slot allocation ----
     # Three pools, by how many top-helicity variants an object carries:
@@ -265,6 +302,7 @@ def build_program(n: int, order: str = "middle") -> Program:
     #      (the helicity of the top for ubar-side objects, of the antitop
     #      for v-side ones)
     #   the bilinear G0 = ubar gamma v                   4 variants, own storage
+    #   A: amplitude accumulators of colour-factor groups  4 variants
     pool_of = {}
     for code, outs, ins, extra in B.ops:
         for o in outs:
@@ -272,6 +310,8 @@ def build_program(n: int, order: str = "middle") -> Program:
                 pool_of[o] = "G"
             elif code == OP_BIL:
                 pool_of[o] = "B"
+            elif code in (OP_AMP_SS, OP_AMP_VV):
+                pool_of[o] = "A"
             else:
                 pool_of[o] = "F"
     last_use = {}
@@ -279,15 +319,15 @@ def build_program(n: int, order: str = "middle") -> Program:
         for o in ins:
             last_use[o] = i
     slot_of = {}
-    free = {"G": [], "F": [], "B": []}
-    nslot = {"G": 0, "F": 0, "B": 0}
+    free = {"G": [], "F": [], "B": [], "A": []}
+    nslot = {"G": 0, "F": 0, "B": 0, "A": 0}
     records = []
     for i, (code, outs, ins, extra) in enumerate(B.ops):
         in_slots = [slot_of[o] for o in ins]
         out_slots = []
         for o in outs:
             pl = pool_of[o]
-            if o not in last_use:
+            if o not in last_use and pl != "A":
                 raise AssertionError("unused wavefunction")
             if free[pl]:
                 free[pl].sort(reverse=True)
@@ -297,15 +337,18 @@ def build_program(n: int, order: str = "middle") -> Program:
                 nslot[pl] += 1
             slot_of[o] = s_
             out_slots.append(s_)
-        # release inputs whose last use is this op (outputs never alias inputs)
-        for o in set(ins):
-            if last_use.get(o) == i:
-                free[pool_of[o]].append(slot_of[o])
+        # release inputs whose last use is this op (outputs never alias inputs);
+        # an accumulator dies at its group's final (scattering) member
+        for o in set(ins) | set(outs):
+            if last_use.get(o, i) == i and (o in ins or (extra and len(extra) == 4 and extra[3] & 8)):
+                if o in slot_of and slot_of[o] not in free[pool_of[o]]:
+                    free[pool_of[o]].append(slot_of[o])
         records.append(_record(code, out_slots, in_slots, extra))
     assert nslot["B"] <= 1
     prog = Program(n=n, npar=n + 2, ncolor=len(perms), ops=records, scatter=scatter,
-                   nslot=nslot["G"], nslot_f=nslot["F"], ndiagrams=P.ndiagrams,
-                   nterms=len(P.diagrams), perms=perms)
+                   nslot=nslot["G"], nslot_f=nslot["F"], nslot_acc=nslot["A"],
+                   ndiagrams=P.ndiagrams, nterms=len(P.diagrams), perms=perms,
+                   ncolour_groups=len(rep))
     return prog
 
 
@@ -327,7 +370,15 @@ def _record(code, outs, ins, extra):
     elif code in (OP_XROW, OP_YCOL, OP_BIL):
         r[1], r[2], r[3] = outs[0], ins[0], ins[1]
     elif code in (OP_AMP_SS, OP_AMP_VV):
+        # [code, -, X, V, scatter offset, scatter count, accumulator (-1: none), mode]
+        # mode: bits 0-1 phase code of this amplitude in its group's sum, bit 2
+        # first member (initialises the accumulator), bit 3 last member (scatters)
         r[2], r[3], r[4], r[5] = ins[0], ins[1], extra[0], extra[1]
+        if extra[2] is None:
+            r[6], r[7] = -1, 0
+        else:
+            r[6] = outs[0] if outs else ins[2]
+            r[7] = extra[3]
     else:
         raise ValueError(code)
     return r

@@ -16,6 +16,7 @@ typedef struct {
     int ngluon, npar, ndiagrams, nterms, ncolor;
     int nslot;               // gluon-wavefunction slots (one variant)
     int nslot_top;           // top-line slots (two helicity variants)
+    int nslot_acc;           // amplitude accumulators of colour-factor groups
     int nops, nscat;
     long long denom;         // colour-matrix common denominator D
     double iden;             // averaging factor

@@ -106,11 +106,21 @@ __device__ __forceinline__ int helicity_index(int g, int bt, int btb) {
 // (pool WF) carry the two helicities of the top (ubar side) or of the antitop
 // (v side); the bilinear G0, the amplitudes and the jamps carry all four.
 // Writes me4[v] = sum_ij D*C_ij Re(J_v,i^* J_v,j).
-template <int NG, int NSG, int NSF, int NC>
+// unit-modulus coefficient {+1, -1, +i, -i}[code] times a
+__device__ __forceinline__ cx unit_times(int code, cx a) {
+    switch (code & 3) {
+        case 0: return a;
+        case 1: return mk(-a.r, -a.i);
+        case 2: return mk(-a.i, a.r);
+        default: return mk(a.i, -a.r);
+    }
+}
+
+template <int NG, int NSG, int NSF, int NSA, int NC>
 __device__ void run_unit(const Kin<NG> &k, int g, const int4 *__restrict__ ops, int nops,
                          const int *__restrict__ scat, const double *__restrict__ cup, double mt,
-                         cx (*WG)[4], cx (*WF)[2][4], cx (*G0)[4], cx (*J)[4], double *me4,
-                         bool colour_sum) {
+                         cx (*WG)[4], cx (*WF)[2][4], cx (*G0)[4], cx (*ACC)[4], cx (*J)[4],
+                         double *me4, bool colour_sum) {
     for (int c = 0; c < NC; c++)
         for (int v = 0; v < 4; v++) J[c][v] = mk(0.0, 0.0);
     for (int i = 0; i < nops; i++) {
@@ -181,6 +191,16 @@ __device__ void run_unit(const Kin<NG> &k, int g, const int4 *__restrict__ ops, 
                             amp[2 * bt + btb] = sdot(WF[a.z][bt], WF[a.w][btb]);
                 } else {
                     for (int v = 0; v < 4; v++) amp[v] = mdot(G0[v], WG[a.w]);
+                }
+                if (b.z >= 0) {  // member of a colour-factor group
+                    const int mode = b.w;
+                    if (mode & 4) {
+                        for (int v = 0; v < 4; v++) ACC[b.z][v] = unit_times(mode, amp[v]);
+                    } else {
+                        for (int v = 0; v < 4; v++) ACC[b.z][v] = ACC[b.z][v] + unit_times(mode, amp[v]);
+                    }
+                    if (!(mode & 8)) break;
+                    for (int v = 0; v < 4; v++) amp[v] = ACC[b.z][v];
                 }
                 const int end = b.x + b.y;
                 for (int s = b.x; s < end; s++) {
@@ -261,7 +281,7 @@ __device__ void write_jamp_rows(const cx (*J)[4], int mask, __nv_bfloat16 *__res
     }
 }
 
-template <int NG, int NSG, int NSF, int NC>
+template <int NG, int NSG, int NSF, int NSA, int NC>
 __global__ void __launch_bounds__(256)
     k_sigmakin(const double *__restrict__ mom, long long nevt, const int4 *__restrict__ ops,
                int nops, const int *__restrict__ scat, const double *__restrict__ cup,
@@ -279,12 +299,14 @@ __global__ void __launch_bounds__(256)
         cx WG[NSG > 0 ? NSG : 1][4];
         cx WF[NSF > 0 ? NSF : 1][2][4];
         cx G0[4][4];
+        cx ACC[NSA][4];
         cx J[NC][4];
         for (int iu = s; iu < nunits; iu += tpe) {
             const int u = __ldg(units + iu);
             const int g = u >> 4, mask = u & 15;
             double me4[4];
-            run_unit<NG, NSG, NSF, NC>(k, g, ops, nops, scat, cup, mt, WG, WF, G0, J, me4, !jout);
+            run_unit<NG, NSG, NSF, NSA, NC>(k, g, ops, nops, scat, cup, mt, WG, WF, G0, ACC, J, me4,
+                                            !jout);
             if (jout) {
                 write_jamp_rows<NC>(J, mask, jout, (e * nunits_pad + iu) * 8, kp);
                 continue;
@@ -305,7 +327,7 @@ __global__ void __launch_bounds__(256)
 // event.  All 32 lanes of a warp call this for the same item (the shuffles
 // below span the warp).  Kept out of line so that the persistent kernel's
 // stack frame is the largest of the carried processes, not their sum.
-template <int NG, int NSG, int NSF, int NC>
+template <int NG, int NSG, int NSF, int NSA, int NC>
 __device__ __noinline__ void batch_slot(const mg_batch_item &it, long long slot) {
     constexpr int NPAR = NG + 2;
     const int tpe = it.tpe;
@@ -318,13 +340,14 @@ __device__ __noinline__ void batch_slot(const mg_batch_item &it, long long slot)
         cx WG[NSG > 0 ? NSG : 1][4];
         cx WF[NSF > 0 ? NSF : 1][2][4];
         cx G0[4][4];
+        cx ACC[NSA][4];
         cx J[NC][4];
         const int4 *ops = reinterpret_cast<const int4 *>(it.ops);
         for (int iu = s; iu < it.nunits; iu += tpe) {
             const int u = __ldg(it.units + iu);
             double me4[4];
-            run_unit<NG, NSG, NSF, NC>(k, u >> 4, ops, it.nops, it.scat, it.cup, it.mt, WG, WF, G0,
-                                       J, me4, true);
+            run_unit<NG, NSG, NSF, NSA, NC>(k, u >> 4, ops, it.nops, it.scat, it.cup, it.mt, WG, WF,
+                                            G0, ACC, J, me4, true);
             for (int v = 0; v < 4; v++)
                 if ((u >> v) & 1) sum += me4[v];
         }
@@ -333,9 +356,9 @@ __device__ __noinline__ void batch_slot(const mg_batch_item &it, long long slot)
     if (e < it.nevt && s == 0) it.me[e] = sum * it.factor;
 }
 
-template <int NG, int NSG, int NSF, int NC>
+template <int NG, int NSG, int NSF, int NSA, int NC>
 __device__ __forceinline__ void batch_dispatch(const mg_batch_item &it, long long slot) {
-    if constexpr (NG <= MG_BATCH_MAX_NGLUON) batch_slot<NG, NSG, NSF, NC>(it, slot);
+    if constexpr (NG <= MG_BATCH_MAX_NGLUON) batch_slot<NG, NSG, NSF, NSA, NC>(it, slot);
 }
 
 // Persistent kernel: every warp repeatedly takes the next 32 slots from the
@@ -354,9 +377,9 @@ __global__ void __launch_bounds__(128, 3)
         const mg_batch_item &it = items[i];
         const long long slot = (long long)base + lane - it.slot_begin;
         switch (it.table_index) {
-#define MG_BATCH_CASE(IDX, NG, NSG, NSF, NC) \
-    case IDX:                                \
-        batch_dispatch<NG, NSG, NSF, NC>(it, slot); \
+#define MG_BATCH_CASE(IDX, NG, NSG, NSF, NSA, NC) \
+    case IDX:                                     \
+        batch_dispatch<NG, NSG, NSF, NSA, NC>(it, slot); \
         break;
             MG_PROC_LIST(MG_BATCH_CASE)
 #undef MG_BATCH_CASE
@@ -392,9 +415,9 @@ cudaError_t mg_launch_sigmakin(const mg_dev_proc &dp, const double *mom, int64_t
     const long long grid = (threads + block - 1) / block;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
     switch (dp.table_index) {
-#define MG_LAUNCH(IDX, NG, NSG, NSF, NC)                                                         \
+#define MG_LAUNCH(IDX, NG, NSG, NSF, NSA, NC)                                                    \
     case IDX:                                                                                    \
-        k_sigmakin<NG, NSG, NSF, NC><<<(unsigned)grid, block, 0, stream>>>(                      \
+        k_sigmakin<NG, NSG, NSF, NSA, NC><<<(unsigned)grid, block, 0, stream>>>(                 \
             mom, nevt, reinterpret_cast<const int4 *>(dp.ops), dp.nops, dp.scat, dp.cup, units,   \
             nunits, tpe, dp.mt, dp.wt, dp.factor, me, me_hel, jout, kp, nunits_pad);              \
         break;
@@ -434,10 +457,10 @@ int mg_sigmakin_occupancy(int table_index, int block, int *ctas_per_sm) {
     int n = 0;
     cudaError_t e = cudaErrorInvalidValue;
     switch (table_index) {
-#define MG_OCC(IDX, NG, NSG, NSF, NC)                                                        \
-    case IDX:                                                                                \
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sigmakin<NG, NSG, NSF, NC>, \
-                                                          block, 0);                         \
+#define MG_OCC(IDX, NG, NSG, NSF, NSA, NC)                                                       \
+    case IDX:                                                                                    \
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sigmakin<NG, NSG, NSF, NSA, NC>, \
+                                                          block, 0);                             \
         break;
         MG_PROC_LIST(MG_OCC)
 #undef MG_OCC

@@ -27,6 +27,8 @@
 
 #include "mg_process.h"
 #include "mgpu.h"
+#include "mgpu_bench.h"
+#include "mgpu_surrogate.h"
 
 using namespace nvcuda;
 

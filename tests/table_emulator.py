@@ -88,7 +88,7 @@ def run(n, mom, mt=173.0, wt=1.4915, alphas=0.118, per_helicity=False):
     mh_all = np.zeros((nev, 1 << npar))
     for h in range(1 << npar):
         sg = lambda ip: 1 if (h >> (npar - 1 - ip)) & 1 else -1
-        WG, WF, WB = {}, {}, {}   # slot pools: gluon, top-line, bilinear
+        WG, WF, WB, WA = {}, {}, {}, {}   # slot pools: gluon, top-line, bilinear, accumulators
         J = np.zeros((nev, prog.ncolor), complex)
         for r in prog.ops:
             c = r[0]
@@ -131,6 +131,12 @@ def run(n, mom, mt=173.0, wt=1.4915, alphas=0.118, per_helicity=False):
                 WB[r[1]] = np.einsum("ei,mij,ej->em", WF[r[2]], _G, WF[r[3]])
             elif c in (P.OP_AMP_SS, P.OP_AMP_VV):
                 a = (WF[r[2]] * WF[r[3]]).sum(-1) if c == P.OP_AMP_SS else _mdot(WB[r[2]], WG[r[3]])
+                if r[6] >= 0:   # colour-factor group: accumulate, last member scatters
+                    ph = [1, -1, 1j, -1j][r[7] & 3]
+                    WA[r[6]] = ph * a if r[7] & 4 else WA[r[6]] + ph * a
+                    if not r[7] & 8:
+                        continue
+                    a = WA[r[6]]
                 for e in prog.scatter[r[4]:r[4] + r[5]]:
                     J[:, e >> 2] += a * [1, -1, 1j, -1j][e & 3]
         mh = np.einsum("ei,ij,ej->e", J.conj(), C, J).real

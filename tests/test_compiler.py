@@ -58,14 +58,16 @@ def test_program_slots_well_formed(n):
     """Every operand is read after it is written, in its own pool, and no
     output overwrites an input of the same operation."""
     prog = program.build_program(n)
-    size = {"G": prog.nslot, "F": prog.nslot_f, "B": 1}
+    size = {"G": prog.nslot, "F": prog.nslot_f, "B": 1, "A": prog.nslot_acc}
     written = set()
     for r in prog.ops:
         outp, ins = _POOLS[r[0]]
         in_keys = [(pl, r[f]) for f, pl in ins]
+        outs = [(pl, r[1 + i]) for i, pl in enumerate(outp)]
+        if r[0] in (program.OP_AMP_SS, program.OP_AMP_VV) and r[6] >= 0:
+            (outs if r[7] & 4 else in_keys).append(("A", r[6]))
         for key in in_keys:
             assert key in written, (r, key)
-        outs = [(pl, r[1 + i]) for i, pl in enumerate(outp)]
         for pl, s in outs:
             assert 0 <= s < size[pl]
             assert (pl, s) not in in_keys
@@ -88,16 +90,20 @@ def test_compiled_tables_match_oracle_on_cpu(ng):
 # ----------------------------------------------------------- C ABI -------
 
 def _header_functions():
-    txt = open(os.path.join(ROOT, "include", "mgpu.h")).read()
-    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(mg_[a-z_]+)\s*\(", txt)))
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names.update(re.findall(r"\b(mg_[a-z0-9_]+)\s*\(", txt))
+    return sorted(names)
 
 
 def test_library_exports_every_declared_symbol():
     from paper_2510_05392_gb300 import binding
     L = binding.lib()
     names = _header_functions()
-    assert len(names) >= 11
+    assert len(names) >= 37
     for name in names:
         assert hasattr(L, name), name
 
@@ -117,3 +123,11 @@ def test_null_arguments_rejected_without_gpu():
     assert L.mg_process_create(None, None, ctypes.byref(h)) == binding.MG_ERR_BAD_ARG
     assert L.mg_sigmakin(None, None, 1, None, None) == binding.MG_ERR_BAD_ARG
     assert L.mg_process_info(None, None) == binding.MG_ERR_BAD_ARG
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5])
+def test_colour_factor_classes_equal_sde_channel_counts(n):
+    """Diagram terms whose colour factors agree up to a phase form as many
+    classes as the paper's table lists single-diagram-enhancement channels."""
+    g = json.load(open(GOLDEN))["processes"]["g g > t t~" + " g" * (n - 2)]
+    assert program.build_program(n).ncolour_groups == g["sde_channels"]

@@ -137,6 +137,41 @@ int mg_sigmakin_hel(mg_process *p, const double *momenta_dev, int64_t nevt, doub
  * MG_OK. */
 int mg_device_status(mg_process *p, void *stream);
 
+/* Per-event extras of sigmaKin (FP64 path; all pointers device, optional
+ * unless stated).  The paper's production kernel also takes an event-by-
+ * event alpha_s, random numbers for a helicity and a colour choice, and a
+ * channel id for single-diagram enhancement (Sec. 2.2):
+ *   alphas_dev       [nevt] per-event alpha_s.  Every vertex is QCD, so
+ *                    |M|^2 scales as alpha_s^ngluon: the matrix element is
+ *                    rescaled by (alphas[e] / params.alphas)^ngluon.
+ *   channel          colour-factor class used as the enhancement channel, or
+ *                    -1.  The classes of diagram terms whose colour factors
+ *                    agree up to a phase are as many as the paper's channels
+ *                    (3 / 15 / 105 / 945); channel c's amplitude is the sum
+ *                    of its class's terms.
+ *   sde_weight_dev   out [nevt] (required when channel >= 0):
+ *                    sum_h |A_c,h|^2 / sum_h sum_c' |A_c',h|^2 (good helicities)
+ *   flow_weight_dev  out [nevt][ncolor]: sum over good helicities of |J_s|^2
+ *                    (jamps without couplings)
+ *   rnd_hel_dev, hel_out_dev   uniforms in [0,1) and out [nevt] helicity index:
+ *                    first h whose running sum of |M_h|^2 exceeds r * sum
+ *   rnd_col_dev, col_out_dev   likewise for the colour flow with weights
+ *                    flow_weight (h and flow choices need their uniforms)
+ * me_out_dev may be NULL.  Uses cached per-process workspaces (grown on
+ * demand). */
+typedef struct {
+    const double *alphas_dev;
+    int channel;
+    double *sde_weight_dev;
+    double *flow_weight_dev;
+    const double *rnd_hel_dev;
+    int *hel_out_dev;
+    const double *rnd_col_dev;
+    int *col_out_dev;
+} mg_sigmakin_extras;
+int mg_sigmakin_ex(mg_process *p, const double *momenta_dev, int64_t nevt,
+                   const mg_sigmakin_extras *extras, double *me_out_dev, void *stream);
+
 /* Launch shape: threads per event (1..32, power of two) and threads per
  * block (multiple of 32, <= 1024).  0 keeps the current value. */
 int mg_set_launch(mg_process *p, int threads_per_event, int block);

@@ -40,6 +40,13 @@ class mg_info(ctypes.Structure):
                 ("flops_colour", ctypes.c_double)]
 
 
+class mg_sigmakin_extras(ctypes.Structure):
+    _fields_ = [("alphas_dev", ctypes.c_void_p), ("channel", ctypes.c_int),
+                ("sde_weight_dev", ctypes.c_void_p), ("flow_weight_dev", ctypes.c_void_p),
+                ("rnd_hel_dev", ctypes.c_void_p), ("hel_out_dev", ctypes.c_void_p),
+                ("rnd_col_dev", ctypes.c_void_p), ("col_out_dev", ctypes.c_void_p)]
+
+
 class MGError(RuntimeError):
     def __init__(self, status, where):
         msg = lib().mg_status_string(status).decode()
@@ -65,6 +72,7 @@ _SIGS = {
     "mg_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "mg_last_cuda_error": ([], ctypes.c_char_p),
     "mg_device_status": ([_VP, _VP], ctypes.c_int),
+    "mg_sigmakin_ex": ([_VP, _VP, ctypes.c_int64, ctypes.POINTER(mg_sigmakin_extras), _VP, _VP], ctypes.c_int),
     "mg_debug_inject_stall": ([_VP, ctypes.c_uint], ctypes.c_int),
     "mg_filter_helicities_noalloc": ([_VP, _VP, ctypes.c_int64, _VP, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "mg_batch_create": ([ctypes.c_int, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_VP), ctypes.POINTER(_VP)], ctypes.c_int),
@@ -158,6 +166,14 @@ class Process:
     def device_status(self, stream=None) -> int:
         """MG_OK or the status of the device-side work issued so far (syncs)."""
         return lib().mg_device_status(self._h, _stream(stream))
+
+    def sigmakin_ex(self, momenta, out=None, alphas=None, channel=-1, sde=None, flow=None,
+                    rnd_hel=None, hel_out=None, rnd_col=None, col_out=None, stream=None):
+        x = mg_sigmakin_extras(_ptr(alphas), channel, _ptr(sde), _ptr(flow), _ptr(rnd_hel),
+                               _ptr(hel_out), _ptr(rnd_col), _ptr(col_out))
+        _check(lib().mg_sigmakin_ex(self._h, _ptr(momenta), momenta.shape[0], ctypes.byref(x),
+                                    _ptr(out), _stream(stream)), "mg_sigmakin_ex")
+        return out
 
     def set_launch(self, threads_per_event=0, block=0):
         _check(lib().mg_set_launch(self._h, threads_per_event, block), "mg_set_launch")

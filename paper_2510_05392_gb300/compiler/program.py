@@ -279,7 +279,7 @@ def build_program(n: int, order: str = "middle") -> Program:
             off = len(scatter)
             for string, c in sorted(d.color.items(), key=lambda kv: pidx[kv[0]]):
                 scatter.append(pidx[string] * 4 + COEF_CODE[complex(c)])
-            B._emit(code, [], ins, [off, len(scatter) - off, None, 0])
+            B._emit(code, [], ins, [off, len(scatter) - off, None, 0, g])
             continue
         first, last = mem[0] == d.idx, mem[-1] == d.idx
         acc_key = ("ACC", g)
@@ -293,7 +293,7 @@ def build_program(n: int, order: str = "middle") -> Program:
                 scatter.append(pidx[string] * 4 + COEF_CODE[complex(c) / c0])
             cnt = len(scatter) - off
         mode = COEF_CODE[phase_of[d.idx]] | (4 if first else 0) | (8 if last else 0)
-        B._emit(code, outs, ins + acc_in, [off, cnt, "acc", mode])
+        B._emit(code, outs, ins + acc_in, [off, cnt, "acc", mode, g])
 
     # ------------------------------------------------ slot allocation ----
     # Three pools, by how many top-helicity variants an object carries:
@@ -340,7 +340,7 @@ def build_program(n: int, order: str = "middle") -> Program:
         # release inputs whose last use is this op (outputs never alias inputs);
         # an accumulator dies at its group's final (scattering) member
         for o in set(ins) | set(outs):
-            if last_use.get(o, i) == i and (o in ins or (extra and len(extra) == 4 and extra[3] & 8)):
+            if last_use.get(o, i) == i and (o in ins or (extra and len(extra) == 5 and extra[3] & 8)):
                 if o in slot_of and slot_of[o] not in free[pool_of[o]]:
                     free[pool_of[o]].append(slot_of[o])
         records.append(_record(code, out_slots, in_slots, extra))
@@ -370,9 +370,11 @@ def _record(code, outs, ins, extra):
     elif code in (OP_XROW, OP_YCOL, OP_BIL):
         r[1], r[2], r[3] = outs[0], ins[0], ins[1]
     elif code in (OP_AMP_SS, OP_AMP_VV):
-        # [code, -, X, V, scatter offset, scatter count, accumulator (-1: none), mode]
+        # [code, class, X, V, scatter offset, scatter count, accumulator (-1: none), mode]
+        # class: the colour-factor class (= single-diagram-enhancement channel)
         # mode: bits 0-1 phase code of this amplitude in its group's sum, bit 2
         # first member (initialises the accumulator), bit 3 last member (scatters)
+        r[1] = extra[4]
         r[2], r[3], r[4], r[5] = ins[0], ins[1], extra[0], extra[1]
         if extra[2] is None:
             r[6], r[7] = -1, 0

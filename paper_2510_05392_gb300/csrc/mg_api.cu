@@ -87,6 +87,8 @@ void free_proc(mg_process *p) {
     cudaFree(p->d_jbuf);
     cudaFree(p->d_part);
     cudaFree(p->d_err);
+    cudaFree(p->d_sel_hel);
+    cudaFree(p->d_sel_jw);
     free(p);
 }
 
@@ -564,5 +566,57 @@ extern "C" int mg_device_status(mg_process *p, void *stream) {
 extern "C" int mg_debug_inject_stall(mg_process *p, unsigned int extra_bytes) {
     if (!p) return MG_ERR_BAD_ARG;
     p->debug_extra_tx = extra_bytes;
+    return MG_OK;
+}
+
+// Per-event extras of the FP64 path (see mgpu.h): running alpha_s, single-
+// diagram-enhancement weight, helicity-summed flow weights, helicity and
+// colour choice.
+extern "C" int mg_sigmakin_ex(mg_process *p, const double *mom, int64_t nevt,
+                              const mg_sigmakin_extras *x, double *me, void *stream) {
+    if (!p || !x || nevt < 0) return MG_ERR_BAD_ARG;
+    if (p->ngood < 0) return MG_ERR_NOT_FILTERED;
+    if (p->par.precision != MG_FP64) return MG_ERR_UNSUPPORTED;
+    if (nevt == 0) return MG_OK;
+    int st = check_dev_ptr(mom, p->device);
+    if (!st && me) st = check_dev_ptr(me, p->device);
+    if (!st && x->alphas_dev) st = check_dev_ptr(x->alphas_dev, p->device);
+    if (!st && x->sde_weight_dev) st = check_dev_ptr(x->sde_weight_dev, p->device);
+    if (!st && x->flow_weight_dev) st = check_dev_ptr(x->flow_weight_dev, p->device);
+    if (st) return st;
+    const bool want_hel = x->hel_out_dev && x->rnd_hel_dev;
+    const bool want_col = x->col_out_dev && x->rnd_col_dev;
+    if ((x->hel_out_dev && !x->rnd_hel_dev) || (x->col_out_dev && !x->rnd_col_dev)) return MG_ERR_BAD_ARG;
+    if (x->channel >= 0 && !x->sde_weight_dev) return MG_ERR_BAD_ARG;
+    if (x->channel < -1) return MG_ERR_BAD_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nhel = 1 << p->tab->npar, nc = p->tab->ncolor;
+    if ((want_hel || (want_col && !x->flow_weight_dev)) && nevt > p->sel_cap) {
+        cudaFree(p->d_sel_hel);
+        cudaFree(p->d_sel_jw);
+        p->d_sel_hel = nullptr;
+        p->d_sel_jw = nullptr;
+        p->sel_cap = 0;
+        cudaError_t e = cudaMalloc(&p->d_sel_hel, sizeof(double) * nevt * nhel);
+        if (e == cudaSuccess) e = cudaMalloc(&p->d_sel_jw, sizeof(double) * nevt * nc);
+        if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? MG_ERR_NO_MEMORY : cuda_fail(e);
+        p->sel_cap = nevt;
+    }
+    double *mh = want_hel ? p->d_sel_hel : nullptr;
+    double *jw = x->flow_weight_dev ? x->flow_weight_dev : (want_col ? p->d_sel_jw : nullptr);
+    if (mh) MG_CUDA(cudaMemsetAsync(mh, 0, sizeof(double) * nevt * nhel, s));
+    mg_extras ex;
+    ex.alphas = x->alphas_dev;
+    ex.alphas0 = p->par.alphas;
+    ex.channel = x->channel;
+    ex.sde = x->channel >= 0 ? x->sde_weight_dev : nullptr;
+    ex.jw = jw;
+    int tpe = p->tpe;
+    while (tpe > 1 && tpe > p->nunits) tpe >>= 1;
+    MG_CUDA(mg_launch_sigmakin(dev_view(p), mom, nevt, p->d_units, p->nunits, tpe, p->block, me, mh, s,
+                               nullptr, 0, 0, &ex));
+    if (want_hel || want_col)
+        MG_CUDA(mg_launch_select(mh, nhel, jw, nc, nevt, x->rnd_hel_dev, x->rnd_col_dev,
+                                 want_hel ? x->hel_out_dev : nullptr, want_col ? x->col_out_dev : nullptr, s));
     return MG_OK;
 }

@@ -63,6 +63,15 @@ typedef struct {
 
 #define MG_TC_ERR_TIMEOUT 1   // device error word: a bounded wait ran out
 
+// Optional per-event extras of the FP64 diagram kernel.
+typedef struct {
+    const double *alphas;  // per-event alpha_s [nevt] or NULL
+    double alphas0;        // alpha_s the couplings were built with
+    int channel;           // single-diagram-enhancement channel (colour-factor class) or -1
+    double *sde;           // out [nevt]: |A_channel|^2 / sum_classes |A|^2 (channel >= 0)
+    double *jw;            // out [nevt][ncolor]: helicity-summed |J_s|^2, or NULL
+} mg_extras;
+
 // One process block of a multi-process batch (device copy read by the
 // persistent kernel).  Slots [slot_begin, slot_end) are event * tpe + thread,
 // padded to a multiple of 32 so that every warp works on one item.
@@ -90,7 +99,10 @@ typedef struct {
 cudaError_t mg_launch_sigmakin(const mg_dev_proc &dp, const double *mom, int64_t nevt,
                                const int *units, int nunits, int tpe, int block, double *me,
                                double *me_hel, cudaStream_t stream, __nv_bfloat16 *jout = nullptr,
-                               int kp = 0, int nunits_pad = 0);
+                               int kp = 0, int nunits_pad = 0, const mg_extras *extras = nullptr);
+cudaError_t mg_launch_select(const double *me_hel, int nhel, const double *jw, int ncolor,
+                             long long nevt, const double *rh, const double *rc, int *hel_out,
+                             int *col_out, cudaStream_t stream);
 cudaError_t mg_launch_helmask(const double *me_hel, int64_t n, int nhel, double rel,
                               unsigned char *mask, cudaStream_t stream);
 // tensor-core colour sum over ncols_alloc (multiple of 128) GEMM rows of jbuf

@@ -120,7 +120,7 @@ template <int NG, int NSG, int NSF, int NSA, int NC>
 __device__ void run_unit(const Kin<NG> &k, int g, const int4 *__restrict__ ops, int nops,
                          const int *__restrict__ scat, const double *__restrict__ cup, double mt,
                          cx (*WG)[4], cx (*WF)[2][4], cx (*G0)[4], cx (*ACC)[4], cx (*J)[4],
-                         double *me4, bool colour_sum) {
+                         double *me4, bool colour_sum, int channel = -1, double *sde8 = nullptr) {
     for (int c = 0; c < NC; c++)
         for (int v = 0; v < 4; v++) J[c][v] = mk(0.0, 0.0);
     for (int i = 0; i < nops; i++) {
@@ -202,6 +202,13 @@ __device__ void run_unit(const Kin<NG> &k, int g, const int4 *__restrict__ ops, 
                     if (!(mode & 8)) break;
                     for (int v = 0; v < 4; v++) amp[v] = ACC[b.z][v];
                 }
+                if (sde8) {  // channel weight: |A_class|^2 over all classes and the chosen one
+                    for (int v = 0; v < 4; v++) {
+                        const double w = fma(amp[v].r, amp[v].r, amp[v].i * amp[v].i);
+                        sde8[4 + v] += w;
+                        if (a.y == channel) sde8[v] += w;
+                    }
+                }
                 const int end = b.x + b.y;
                 for (int s = b.x; s < end; s++) {
                     const int e = __ldg(scat + s);
@@ -281,18 +288,30 @@ __device__ void write_jamp_rows(const cx (*J)[4], int mask, __nv_bfloat16 *__res
     }
 }
 
-template <int NG, int NSG, int NSF, int NSA, int NC>
+template <int NG, int NSG, int NSF, int NSA, int NC, bool EX>
 __global__ void __launch_bounds__(256)
     k_sigmakin(const double *__restrict__ mom, long long nevt, const int4 *__restrict__ ops,
                int nops, const int *__restrict__ scat, const double *__restrict__ cup,
                const int *__restrict__ units, int nunits, int tpe, double mt, double wt,
                double factor, double *__restrict__ me, double *__restrict__ me_hel,
-               __nv_bfloat16 *__restrict__ jout, int kp, int nunits_pad) {
+               __nv_bfloat16 *__restrict__ jout, int kp, int nunits_pad, mg_extras ex) {
     constexpr int NPAR = NG + 2;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long e = t / tpe;
     const int s = (int)(t - e * tpe);
     double sum = 0.0;
+    // per-event extras (compiled only into the EX instantiation)
+    double sde8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double num = 0.0, den = 0.0;
+    double jw[EX ? NC : 1];
+    if (EX && ex.jw)
+        for (int c = 0; c < NC; c++) jw[c] = 0.0;
+    if (EX && ex.alphas && e < nevt) {  // per-event strong coupling: |M|^2 ~ alpha_s^NG
+        const double r = ex.alphas[e] / ex.alphas0;
+        double f = 1.0;
+        for (int i = 0; i < NG; i++) f *= r;
+        factor *= f;
+    }
     if (e < nevt) {
         Kin<NG> k;
         kinematics<NG>(k, mom + e * (NPAR * 4), mt, wt);
@@ -305,8 +324,10 @@ __global__ void __launch_bounds__(256)
             const int u = __ldg(units + iu);
             const int g = u >> 4, mask = u & 15;
             double me4[4];
+            if (EX)
+                for (int q = 0; q < 8; q++) sde8[q] = 0.0;
             run_unit<NG, NSG, NSF, NSA, NC>(k, g, ops, nops, scat, cup, mt, WG, WF, G0, ACC, J, me4,
-                                            !jout);
+                                            !jout, ex.channel, (EX && ex.sde) ? sde8 : nullptr);
             if (jout) {
                 write_jamp_rows<NC>(J, mask, jout, (e * nunits_pad + iu) * 8, kp);
                 continue;
@@ -314,12 +335,74 @@ __global__ void __launch_bounds__(256)
             for (int v = 0; v < 4; v++) {
                 if (!((mask >> v) & 1)) continue;
                 sum += me4[v];
+                if (EX) {
+                    num += sde8[v];
+                    den += sde8[4 + v];
+                    if (ex.jw)
+                        for (int c = 0; c < NC; c++)
+                            jw[c] = fma(J[c][v].r, J[c][v].r, fma(J[c][v].i, J[c][v].i, jw[c]));
+                }
                 if (me_hel) me_hel[e * (1LL << NPAR) + helicity_index<NG>(g, v >> 1, v & 1)] = me4[v] * factor;
             }
         }
     }
-    for (int o = tpe >> 1; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if (e < nevt && s == 0 && me) me[e] = sum * factor;
+    for (int o = tpe >> 1; o > 0; o >>= 1) {
+        sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (EX && ex.sde) {
+            num += __shfl_xor_sync(0xffffffffu, num, o);
+            den += __shfl_xor_sync(0xffffffffu, den, o);
+        }
+        if (EX && ex.jw)
+            for (int c = 0; c < NC; c++) jw[c] += __shfl_xor_sync(0xffffffffu, jw[c], o);
+    }
+    if (e < nevt && s == 0) {
+        if (me) me[e] = sum * factor;
+        if (EX && ex.sde) ex.sde[e] = den > 0.0 ? num / den : 0.0;
+        if (EX && ex.jw)
+            for (int c = 0; c < NC; c++) ex.jw[e * NC + c] = jw[c];
+    }
+}
+
+// Helicity and colour-flow choice per event (the other output of the
+// paper's sigmaKin, Sec. 2.2): h is the first index whose running sum of
+// |M_h|^2 exceeds r_hel times the total, the flow likewise from the
+// helicity-summed |J_s|^2.
+__global__ void k_select(const double *__restrict__ me_hel, int nhel, const double *__restrict__ jw,
+                         int ncolor, long long nevt, const double *__restrict__ rh,
+                         const double *__restrict__ rc, int *__restrict__ hel_out,
+                         int *__restrict__ col_out) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nevt) return;
+    if (hel_out && rh) {
+        const double *w = me_hel + e * nhel;
+        double tot = 0.0;
+        for (int h = 0; h < nhel; h++) tot += w[h];
+        const double cut = rh[e] * tot;
+        double run = 0.0;
+        int pick = -1;
+        for (int h = 0; h < nhel; h++) {
+            if (w[h] <= 0.0) continue;
+            run += w[h];
+            pick = h;
+            if (run > cut) break;
+        }
+        hel_out[e] = pick;
+    }
+    if (col_out && rc) {
+        const double *w = jw + e * ncolor;
+        double tot = 0.0;
+        for (int c = 0; c < ncolor; c++) tot += w[c];
+        const double cut = rc[e] * tot;
+        double run = 0.0;
+        int pick = -1;
+        for (int c = 0; c < ncolor; c++) {
+            if (w[c] <= 0.0) continue;
+            run += w[c];
+            pick = c;
+            if (run > cut) break;
+        }
+        col_out[e] = pick;
+    }
 }
 
 // ------------------------------------------------ multi-process batch ----
@@ -409,7 +492,17 @@ __global__ void k_helmask(const double *__restrict__ mh, long long n, int nhel, 
 cudaError_t mg_launch_sigmakin(const mg_dev_proc &dp, const double *mom, int64_t nevt,
                                const int *units, int nunits, int tpe, int block, double *me,
                                double *me_hel, cudaStream_t stream, __nv_bfloat16 *jout, int kp,
-                               int nunits_pad) {
+                               int nunits_pad, const mg_extras *extras) {
+    mg_extras ex;
+    if (extras) {
+        ex = *extras;
+    } else {
+        ex.alphas = nullptr;
+        ex.alphas0 = 1.0;
+        ex.channel = -1;
+        ex.sde = nullptr;
+        ex.jw = nullptr;
+    }
     if (nevt <= 0) return cudaSuccess;
     const long long threads = (long long)nevt * tpe;
     const long long grid = (threads + block - 1) / block;
@@ -417,9 +510,14 @@ cudaError_t mg_launch_sigmakin(const mg_dev_proc &dp, const double *mom, int64_t
     switch (dp.table_index) {
 #define MG_LAUNCH(IDX, NG, NSG, NSF, NSA, NC)                                                    \
     case IDX:                                                                                    \
-        k_sigmakin<NG, NSG, NSF, NSA, NC><<<(unsigned)grid, block, 0, stream>>>(                 \
-            mom, nevt, reinterpret_cast<const int4 *>(dp.ops), dp.nops, dp.scat, dp.cup, units,   \
-            nunits, tpe, dp.mt, dp.wt, dp.factor, me, me_hel, jout, kp, nunits_pad);              \
+        if (extras)                                                                              \
+            k_sigmakin<NG, NSG, NSF, NSA, NC, true><<<(unsigned)grid, block, 0, stream>>>(       \
+                mom, nevt, reinterpret_cast<const int4 *>(dp.ops), dp.nops, dp.scat, dp.cup,      \
+                units, nunits, tpe, dp.mt, dp.wt, dp.factor, me, me_hel, jout, kp, nunits_pad, ex); \
+        else                                                                                     \
+            k_sigmakin<NG, NSG, NSF, NSA, NC, false><<<(unsigned)grid, block, 0, stream>>>(      \
+                mom, nevt, reinterpret_cast<const int4 *>(dp.ops), dp.nops, dp.scat, dp.cup,      \
+                units, nunits, tpe, dp.mt, dp.wt, dp.factor, me, me_hel, jout, kp, nunits_pad, ex); \
         break;
         MG_PROC_LIST(MG_LAUNCH)
 #undef MG_LAUNCH
@@ -459,7 +557,7 @@ int mg_sigmakin_occupancy(int table_index, int block, int *ctas_per_sm) {
     switch (table_index) {
 #define MG_OCC(IDX, NG, NSG, NSF, NSA, NC)                                                       \
     case IDX:                                                                                    \
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sigmakin<NG, NSG, NSF, NSA, NC>, \
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sigmakin<NG, NSG, NSF, NSA, NC, false>, \
                                                           block, 0);                             \
         break;
         MG_PROC_LIST(MG_OCC)
@@ -470,4 +568,13 @@ int mg_sigmakin_occupancy(int table_index, int block, int *ctas_per_sm) {
     if (e != cudaSuccess) return MG_ERR_CUDA;
     *ctas_per_sm = n > 0 ? n : 1;
     return MG_OK;
+}
+
+cudaError_t mg_launch_select(const double *me_hel, int nhel, const double *jw, int ncolor,
+                             long long nevt, const double *rh, const double *rc, int *hel_out,
+                             int *col_out, cudaStream_t stream) {
+    if (nevt <= 0) return cudaSuccess;
+    k_select<<<(unsigned)((nevt + 127) / 128), 128, 0, stream>>>(me_hel, nhel, jw, ncolor, nevt, rh, rc,
+                                                               hel_out, col_out);
+    return cudaGetLastError();
 }

@@ -30,6 +30,10 @@ struct mg_process {
     long long part_len;
     int *d_err;                  // device error word of the bounded waits
     uint32_t debug_extra_tx;     // test hook: extra bytes the TMA barrier expects
+    // per-event extras (mg_sigmakin_ex): cached workspaces
+    double *d_sel_hel;           // [cap][2^npar] per-helicity |M_h|^2
+    double *d_sel_jw;            // [cap][ncolor] helicity-summed |J_s|^2
+    long long sel_cap;
 };
 
 // helpers of mg_api.cu used by the other host files

@@ -330,7 +330,10 @@ def run_surrogate(args):
     wts = wt.cpu().numpy()
     nacc = int((acc.cpu().numpy() != 0).sum())
     kish = float(wts.sum() ** 2 / max((wts ** 2).sum(), 1e-300))
-    eff_plain = float(w_tr.mean() / w_tr.max())          # hit-or-miss with w_max of the same slice
+    # plain hit-or-miss with the same convention as the two-stage rule: the
+    # maximum is the 0.999 quantile of the slice, larger weights kept as overweights
+    w_q = float(np.quantile(w_tr, 0.999))
+    eff_plain = float(np.mean(np.minimum(1.0, w_tr / w_q)))
     plain_unw_per_s = rate_exact * eff_plain
     two_unw_per_s = nacc / t_two
     line = {
@@ -346,7 +349,8 @@ def run_surrogate(args):
         "two_stage": {"seconds": t_two, "exact_evaluations": int(nex.value), "accepted": nacc,
                       "what_max": what_max, "r_max": r_max, "kish_ess": kish,
                       "unweighted_events_per_s": two_unw_per_s},
-        "plain_hit_or_miss": {"efficiency": eff_plain, "unweighted_events_per_s": plain_unw_per_s},
+        "plain_hit_or_miss": {"efficiency": eff_plain, "w_max_quantile": w_q,
+                              "unweighted_events_per_s": plain_unw_per_s},
         "surrogate_gain_unweighted_events_per_s": two_unw_per_s / plain_unw_per_s,
         "gpu_launches": None,
     }

@@ -45,6 +45,23 @@ WORKLOADS = {
 TEST_SEED = 12345  # helicity-filter test events
 
 
+def shard_first_candidate(rank: int) -> int:
+    """First generator candidate of a rank: ranks draw disjoint candidate
+    ranges of the same seeded generator (rank 0 = the standard workload)."""
+    return rank * (1 << 40)
+
+
+def max_over_ranks(t: float, device=None) -> float:
+    """Slowest rank's time (all ranks call it; identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return t
+    tt = torch.tensor([t], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return tt.item()
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -375,7 +392,7 @@ def run_ours(args):
     npar = ng + 4
     # each rank evaluates its own nevt events (weak scaling; rank 0 holds the
     # standard workload, rank r the next candidates of the same generator)
-    mom_h = _events(name, nevt, first_candidate=rank * (1 << 40))
+    mom_h = _events(name, nevt, first_candidate=shard_first_candidate(rank))
     mom = torch.from_numpy(mom_h).to(dev)
     out = torch.empty(nevt, dtype=torch.float64, device=dev)
     prec = binding.MG_MIXED_BF16 if args.precision == "mixed" else binding.MG_FP64
@@ -417,11 +434,7 @@ def run_ours(args):
         torch.distributed.barrier()
     clk = clocks.stop() if clocks else None
     launch_ms = [a.elapsed_time(b) for a, b in ev]
-    t_dev = sum(launch_ms) / 1e3
-    if ws > 1:
-        tt = torch.tensor([t_dev], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_dev = tt.item()
+    t_dev = max_over_ranks(sum(launch_ms) / 1e3, dev)
     value = ws * nevt * args.steps / t_dev
     ms_step = 1e3 * t_dev / args.steps
 
@@ -453,11 +466,7 @@ def run_ours(args):
             host_out.copy_(out, non_blocking=True)
         b.record(stream)
         torch.cuda.synchronize(dev)
-        te = a.elapsed_time(b) / 1e3
-        if ws > 1:
-            tt = torch.tensor([te], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            te = tt.item()
+        te = max_over_ranks(a.elapsed_time(b) / 1e3, dev)
         e2e = {"value": ws * nevt * args.steps / te, "unit": "events/s",
                "h2d_bytes_per_step": nevt * npar * 4 * 8, "d2h_bytes_per_step": nevt * 8}
         assert torch.isfinite(host_out).all().item()

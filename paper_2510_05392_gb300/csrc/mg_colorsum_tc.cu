@@ -125,121 +125,218 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *r) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__global__ void __launch_bounds__(128, 1)
+// Warp-specialised persistent kernel (192 threads):
+//   warp 0  TMA producer: the two colour-matrix halves once, then the A chunks
+//           (one split x 64 colours x 128 rows, 16 KiB) of every tile through
+//           a ring of TC_STAGES shared-memory stages (full/empty mbarriers);
+//   warp 1  MMA issuer (one thread): per chunk 4 (hi) or 8 (hi + lo colour
+//           matrix) tcgen05.mma, then tcgen05.commit to free the stage; per
+//           tile a commit to the accumulator's "full" barrier; two TMEM
+//           accumulators alternate so the next tile's MMAs overlap this
+//           tile's epilogue;
+//   warps 2-5 epilogue: each thread owns one row (TMEM lane 32 (warp % 4) +
+//           lane), reads its row of Z and forms sum_n V Z in compensated FP32
+//           (exact products, two-sum accumulation, ~48 significant bits),
+//           then the event groups are summed in shared memory in a fixed order.
+constexpr int TC_STAGES = 6;
+constexpr int TC_THREADS = 192;
+
+struct TcSmem {
+    uint64_t *bB, *full, *empty, *tfull, *tempty;
+    uint32_t *tmem_slot;
+    int *failed;
+    double *colsum;
+};
+
+__device__ __forceinline__ void tc_fail(int *failed, int *err) {
+    atomicExch(failed, 1);
+    atomicExch(err, MG_TC_ERR_TIMEOUT);
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
     k_colorsum_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                  const __nv_bfloat16 *__restrict__ jbuf, int kp, int np, int ncolor, int cpe,
-                  int tmem_cols, uint32_t extra_tx, double *__restrict__ part, int *__restrict__ err) {
+                  const __nv_bfloat16 *__restrict__ jbuf, int kp, int np, int np_pad, int ncolor,
+                  int cpe, long long ntiles, int tmem_cols, uint32_t extra_tx,
+                  double *__restrict__ part, int *__restrict__ err) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int kc_n = kp / TC_KCHUNK;
-    const int a_chunk = TC_M * 128;   // bytes per A chunk (128 rows x 128 B)
-    const int b_chunk = np * 128;     // bytes per B chunk
-    unsigned char *sA = smem;                                  // [3][kc_n] chunks
-    unsigned char *sB = sA + 3 * kc_n * a_chunk;               // [2][kc_n] chunks
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sB + 2 * kc_n * b_chunk);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2);
-    double *colsum = reinterpret_cast<double *>(bars + 4);
+    const int nchunk = 3 * kc_n;                // A chunks per tile: split-major
+    const int a_chunk = TC_M * 128;
+    const int b_chunk = np * 128;
+    unsigned char *sB = smem;                   // [2][kc_n] chunks, resident
+    unsigned char *sA = sB + 2 * kc_n * b_chunk;  // [TC_STAGES] chunks
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sA + TC_STAGES * a_chunk);
+    TcSmem S;
+    S.bB = bars;
+    S.full = bars + 1;
+    S.empty = S.full + TC_STAGES;
+    S.tfull = S.empty + TC_STAGES;
+    S.tempty = S.tfull + 2;
+    S.tmem_slot = reinterpret_cast<uint32_t *>(S.tempty + 2);
+    S.failed = reinterpret_cast<int *>(S.tmem_slot + 1);
+    S.colsum = reinterpret_cast<double *>(S.tmem_slot + 2);
 
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const long long m0 = (long long)blockIdx.x * TC_M;
-
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         smem_u32(tmem_slot)),
+                         smem_u32(S.tmem_slot)),
                      "r"(tmem_cols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 32) {
-        mbar_init(&bars[0], 1);  // operands landed
-        mbar_init(&bars[1], 1);  // accumulator ready
+        mbar_init(S.bB, 1);
+        for (int i = 0; i < TC_STAGES; i++) {
+            mbar_init(&S.full[i], 1);
+            mbar_init(&S.empty[i], 1);
+        }
+        for (int i = 0; i < 2; i++) {
+            mbar_init(&S.tfull[i], 1);
+            mbar_init(&S.tempty[i], 4);   // one arrival per epilogue warp
+        }
+        *S.failed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = *tmem_slot;
+    const uint32_t tmem = *S.tmem_slot;
 
-    const uint32_t bytes = (uint32_t)(3 * kc_n * a_chunk + 2 * kc_n * b_chunk);
-    bool ok = true;
-    if (tid == 0) {
-        mbar_expect_tx(&bars[0], bytes + extra_tx);
-        for (int s = 0; s < 3; s++)
-            for (int kc = 0; kc < kc_n; kc++)
-                tma_load_2d(sA + (s * kc_n + kc) * a_chunk, &tmA, s * kp + kc * TC_KCHUNK, (int)m0,
-                            &bars[0]);
-        for (int h = 0; h < 2; h++)
-            for (int kc = 0; kc < kc_n; kc++)
-                tma_load_2d(sB + (h * kc_n + kc) * b_chunk, &tmB, kc * TC_KCHUNK, h * np, &bars[0]);
-        ok = mbar_wait(&bars[0], 0, TC_WAIT_CYCLES);
-        if (ok) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t idesc = instr_desc(TC_M, np);
-            uint32_t acc = 0;
-            // V_{hi,mid,lo} C_hi, then V_{hi,mid} C_lo; K = 16 per instruction
-            for (int pass = 0; pass < 2; pass++) {
-                const int nsplit = pass == 0 ? 3 : 2;
-                for (int s = 0; s < nsplit; s++)
-                    for (int kc = 0; kc < kc_n; kc++) {
-                        const uint32_t a0 = smem_u32(sA + (s * kc_n + kc) * a_chunk);
-                        const uint32_t b0 = smem_u32(sB + (pass * kc_n + kc) * b_chunk);
-                        for (int k = 0; k < TC_KCHUNK / 16; k++) {
-                            mma_bf16(tmem, smem_desc(a0 + 32 * k), smem_desc(b0 + 32 * k), idesc, acc);
-                            acc = 1;
-                        }
+    if (warp == 0) {
+        if (lane == 0) {  // ------------------------------------ producer
+            mbar_expect_tx(S.bB, (uint32_t)(2 * kc_n * b_chunk));
+            for (int h = 0; h < 2; h++)
+                for (int kc = 0; kc < kc_n; kc++)
+                    tma_load_2d(sB + (h * kc_n + kc) * b_chunk, &tmB, kc * TC_KCHUNK, h * np, S.bB);
+            int stage = 0;
+            uint32_t phase = 0;
+            for (long long t = blockIdx.x; t < ntiles && !*(volatile int *)S.failed; t += gridDim.x) {
+                for (int c = 0; c < nchunk; c++) {
+                    if (!mbar_wait(&S.empty[stage], phase ^ 1, TC_WAIT_CYCLES)) {
+                        tc_fail(S.failed, err);
+                        break;
                     }
+                    mbar_expect_tx(&S.full[stage], (uint32_t)a_chunk + extra_tx);
+                    const int sp = c / kc_n, kc = c % kc_n;
+                    tma_load_2d(sA + stage * a_chunk, &tmA, sp * kp + kc * TC_KCHUNK, (int)(t * TC_M),
+                                &S.full[stage]);
+                    if (++stage == TC_STAGES) {
+                        stage = 0;
+                        phase ^= 1;
+                    }
+                }
             }
-            mma_commit(&bars[1]);
-        } else {
-            atomicExch(err, MG_TC_ERR_TIMEOUT);
-            // let copies still in flight land before the CTA's memory goes away
-            mbar_wait(&bars[0], 0, TC_WAIT_CYCLES >> 2);
         }
-    }
-    __syncthreads();
-    ok = (tid == 0) ? ok : true;
-    // every thread waits for the accumulator (bounded); a CTA whose loads timed
-    // out never commits, so its threads skip the wait through the flag below
-    __shared__ int s_failed;
-    if (tid == 0) s_failed = ok ? 0 : 1;
-    __syncthreads();
-    double acc = 0.0;
-    if (!s_failed) {
-        // warp-uniform decision: tcgen05.ld below is a warp-collective instruction
-        const bool landed = __all_sync(0xffffffffu, mbar_wait(&bars[1], 0, TC_WAIT_CYCLES));
-        if (!landed) {
-            atomicExch(err, MG_TC_ERR_TIMEOUT);
-        } else {
+    } else if (warp == 1) {
+        if (lane == 0) {  // ------------------------------------ MMA issuer
+            bool ok = mbar_wait(S.bB, 0, TC_WAIT_CYCLES);
+            if (!ok) tc_fail(S.failed, err);
+            const uint32_t idesc = instr_desc(TC_M, np);
+            int stage = 0;
+            uint32_t phase = 0, aphase = 0;
+            int acc = 0;
+            for (long long t = blockIdx.x; ok && t < ntiles && !*(volatile int *)S.failed; t += gridDim.x) {
+                if (!mbar_wait(&S.tempty[acc], aphase ^ 1, TC_WAIT_CYCLES)) {
+                    tc_fail(S.failed, err);
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t d = tmem + (uint32_t)(acc * np_pad);
+                uint32_t accumulate = 0;
+                for (int c = 0; c < nchunk; c++) {
+                    if (!mbar_wait(&S.full[stage], phase, TC_WAIT_CYCLES)) {
+                        tc_fail(S.failed, err);
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const int sp = c / kc_n, kc = c % kc_n;
+                    const uint32_t a0 = smem_u32(sA + stage * a_chunk);
+                    const uint32_t bh = smem_u32(sB + kc * b_chunk);
+                    const uint32_t bl = smem_u32(sB + (kc_n + kc) * b_chunk);
+                    for (int k = 0; k < TC_KCHUNK / 16; k++) {
+                        mma_bf16(d, smem_desc(a0 + 32 * k), smem_desc(bh + 32 * k), idesc, accumulate);
+                        accumulate = 1;
+                    }
+                    if (sp < 2)  // V_hi C_lo, V_mid C_lo (V_lo C_lo dropped)
+                        for (int k = 0; k < TC_KCHUNK / 16; k++)
+                            mma_bf16(d, smem_desc(a0 + 32 * k), smem_desc(bl + 32 * k), idesc, 1);
+                    mma_commit(&S.empty[stage]);
+                    if (++stage == TC_STAGES) {
+                        stage = 0;
+                        phase ^= 1;
+                    }
+                }
+                if (!ok) break;
+                mma_commit(&S.tfull[acc]);
+                if (++acc == 2) {
+                    acc = 0;
+                    aphase ^= 1;
+                }
+            }
+        }
+    } else {  // ------------------------------------------------ epilogue
+        const int quarter = warp & 3;
+        const int m = quarter * 32 + lane;      // tile row this thread owns
+        const int et = tid - 64;                // 0..127 among epilogue threads
+        int acc = 0;
+        uint32_t aphase = 0;
+        const int gsize = cpe < TC_M ? cpe : TC_M;
+        const int ngroups = TC_M / gsize;
+        for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            const bool landed =
+                __all_sync(0xffffffffu, !*(volatile int *)S.failed &&
+                                            mbar_wait(&S.tfull[acc], aphase, TC_WAIT_CYCLES));
+            if (!landed) {
+                if (lane == 0) tc_fail(S.failed, err);
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const __nv_bfloat16 *row = jbuf + (m0 + tid) * (long long)(3 * kp);
-            const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+            const __nv_bfloat16 *row = jbuf + (t * TC_M + m) * (long long)(3 * kp);
+            const uint32_t taddr = tmem + (uint32_t)(acc * np_pad) + ((uint32_t)(quarter * 32) << 16);
+            float sh = 0.0f, sl = 0.0f;
             for (int c0 = 0; c0 < np; c0 += 16) {
                 uint32_t z[16];
-                tmem_ld16(lane_addr + (uint32_t)c0, z);
+                tmem_ld16(taddr + (uint32_t)c0, z);
 #pragma unroll
                 for (int j = 0; j < 16; j++) {
                     const int n = c0 + j;
                     if (n < ncolor) {
                         const float v = __bfloat162float(row[n]) + __bfloat162float(row[kp + n]) +
                                         __bfloat162float(row[2 * kp + n]);
-                        acc = fma((double)v, (double)__uint_as_float(z[j]), acc);
+                        const float zz = __uint_as_float(z[j]);
+                        const float p = v * zz;
+                        const float pe = fmaf(v, zz, -p);       // exact product p + pe
+                        const float s = sh + p;                  // two-sum (sh, p)
+                        const float bp = s - sh;
+                        const float se = (sh - (s - bp)) + (p - bp);
+                        sh = s;
+                        sl += se + pe;
                     }
                 }
             }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&S.tempty[acc])) : "memory");
+            S.colsum[m] = (double)sh + (double)sl;
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            if (et < ngroups) {
+                double sum = 0.0;
+                for (int j = 0; j < gsize; j++) sum += S.colsum[et * gsize + j];
+                part[t * ngroups + et] = sum;
+            }
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            if (++acc == 2) {
+                acc = 0;
+                aphase ^= 1;
+            }
         }
     }
-    colsum[tid] = acc;
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    // fixed-order reduction of each event group of cpe columns inside the tile
-    const int gsize = cpe < TC_M ? cpe : TC_M;
-    const int ngroups = TC_M / gsize;
-    if (tid < ngroups) {
-        double s = 0.0;
-        for (int j = 0; j < gsize; j++) s += colsum[tid * gsize + j];
-        part[blockIdx.x * (long long)ngroups + tid] = s;
-    }
     if (warp == 0) {
+        __syncwarp();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(tmem_cols)
                      : "memory");
@@ -291,26 +388,32 @@ bool make_map(CUtensorMap *m, const void *base, uint64_t rows, uint64_t cols, ui
 
 size_t mg_tc_smem_bytes(int kp, int np) {
     const int kc_n = kp / TC_KCHUNK;
-    return 1024 + (size_t)3 * kc_n * TC_M * 128 + (size_t)2 * kc_n * np * 128 + 4 * 8 + TC_M * 8;
+    return 1024 + (size_t)2 * kc_n * np * 128 + (size_t)TC_STAGES * TC_M * 128 +
+           (1 + 2 * TC_STAGES + 4) * 8 + 16 + TC_M * 8;
 }
 
 cudaError_t mg_launch_colorsum_tc(const __nv_bfloat16 *jbuf, long long ncols_alloc, int kp,
                                   const __nv_bfloat16 *cmat, int np, int ncolor, int cpe,
                                   uint32_t extra_tx, double *part, int *err, cudaStream_t stream) {
-    if (ncols_alloc % TC_M || kp % TC_KCHUNK || np % 16 || np > 256 || kp > 256)
+    if (ncols_alloc % TC_M || kp % TC_KCHUNK || np % 16 || np > 128 || kp > 256)
         return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
     if (!make_map(&ma, jbuf, (uint64_t)ncols_alloc, (uint64_t)3 * kp, TC_M)) return cudaErrorInvalidValue;
     if (!make_map(&mb, cmat, (uint64_t)2 * np, (uint64_t)kp, (uint32_t)np)) return cudaErrorInvalidValue;
-    int tmem_cols = 32;
-    while (tmem_cols < np) tmem_cols <<= 1;
+    int np_pad = 32;
+    while (np_pad < np) np_pad <<= 1;
+    const int tmem_cols = 2 * np_pad;  // two accumulators
     const size_t smem = mg_tc_smem_bytes(kp, np);
     cudaError_t e = cudaFuncSetAttribute(k_colorsum_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    const long long grid = ncols_alloc / TC_M;
-    k_colorsum_tc<<<(unsigned)grid, TC_M, smem, stream>>>(ma, mb, jbuf, kp, np, ncolor, cpe,
-                                                           tmem_cols, extra_tx, part, err);
+    int dev = 0, nsm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const long long ntiles = ncols_alloc / TC_M;
+    const long long grid = ntiles < nsm ? ntiles : nsm;   // persistent: one CTA per SM
+    k_colorsum_tc<<<(unsigned)grid, TC_THREADS, smem, stream>>>(ma, mb, jbuf, kp, np, np_pad, ncolor,
+                                                                cpe, ntiles, tmem_cols, extra_tx, part, err);
     return cudaGetLastError();
 }
 

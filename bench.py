@@ -126,25 +126,47 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def _kernel_hash():
+_FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def _measured_peak(key):
+    """Measured peak of this GPU pool (copy GB/s, cuBLAS bf16 TFLOP/s), else
+    the fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)[key])
+    except (OSError, ValueError, KeyError, TypeError):
+        return _FALLBACK_PEAKS.get(key)
+
+
+_KERNEL_SOURCES = {
+    "k_sigmakin": ["mg_kernels.cu", "mg_dirac.cuh", "mg_internal.h"],
+    "k_colorsum_tc": ["mg_colorsum_tc.cu", "mg_internal.h"],
+}
+
+
+def _kernel_hash(kernel="k_sigmakin"):
     h = hashlib.sha256()
-    for f in ["mg_kernels.cu", "mg_dirac.cuh", "mg_internal.h"]:
+    for f in _KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_2510_05392_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def _traffic(kernel, workload):
+def _traffic(kernel, workload, events_per_launch=None):
     """DRAM bytes per launch from the committed ncu summary, when it was
-    taken on the current kernel sources (else None)."""
+    taken on the current kernel sources (else None); entries stored per event
+    are scaled to events_per_launch."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         data = json.load(open(path))
     except (OSError, ValueError):
         return None
     e = data.get(f"{kernel}:{workload}")
-    if not e or e.get("kernel_hash") != _kernel_hash():
+    if not e or e.get("kernel_hash") != _kernel_hash(kernel):
         return None
+    if "dram_bytes_per_event" in e and events_per_launch:
+        return e["dram_bytes_per_event"] * events_per_launch
     return e.get("dram_bytes_per_launch")
 
 
@@ -419,6 +441,9 @@ def run_ours(args):
     clocks = Clocks(local) if (rank == 0 and not args.no_clocks) else None
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
+    # per-kernel CUDA events on the launching stream, recorded by the library
+    p.set_kernel_timing(args.steps * 3 * 256)
+    p.kernel_times(reset=True)
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
@@ -433,18 +458,36 @@ def run_ours(args):
     if ws > 1:
         torch.distributed.barrier()
     clk = clocks.stop() if clocks else None
+    kt = p.kernel_times(reset=True)
+    p.set_kernel_timing(0)
     launch_ms = [a.elapsed_time(b) for a, b in ev]
     t_dev = max_over_ranks(sum(launch_ms) / 1e3, dev)
     value = ws * nevt * args.steps / t_dev
     ms_step = 1e3 * t_dev / args.steps
+    n_launches = sum(n for _, n in kt.values())
 
-    # algorithmic FP64 work of one launch
-    # (mixed: the colour sum runs on the tensor cores, so only the diagram
-    # work is FP64; the timed step then also holds the colour-sum kernels,
-    # which makes the FP64 fraction a lower bound for the diagram kernel)
+    # algorithmic FP64 work of the diagram kernel per step (mixed: the colour
+    # sum runs on the tensor cores, so only the diagram work is FP64), over
+    # the diagram kernel's own device time
     fp64_colour = info.flops_colour if args.precision == "fp64" else 0.0
-    flops_launch = nevt * ngood * (info.flops_diagram + fp64_colour)
-    achieved = flops_launch / (statistics.mean(launch_ms) / 1e3)
+    flops_step = nevt * ngood * (info.flops_diagram + fp64_colour)
+    diag_ms, diag_n = kt["diagram"]
+    per_step = diag_n // args.steps
+    achieved = flops_step * args.steps / (diag_ms / 1e3)
+    roof_tc = None
+    if args.precision == "mixed":
+        # tensor-core colour sum: bound by reading the BF16 jamp pieces once,
+        # 2 (re, im) x 3 pieces x ncolor x 2 bytes per event and good helicity
+        tc_ms, tc_n = kt["colour_tc"]
+        bytes_step = nevt * ngood * 2 * 3 * info.ncolor * 2
+        tc_ach = bytes_step * args.steps / (tc_ms / 1e3) / 1e9
+        hbm = _measured_peak("hbm_gbs")
+        roof_tc = {"bound": "hbm", "achieved": tc_ach, "peak": hbm, "unit": "GB/s",
+                   "frac": tc_ach / hbm if hbm else None,
+                   "traffic": _traffic("k_colorsum_tc", name, nevt * args.steps / tc_n),
+                   "kernel": "k_colorsum_tc (peak = measured copy bandwidth)",
+                   "launches_per_step": tc_n // args.steps,
+                   "ms_per_step": tc_ms / args.steps, "bytes_per_step": bytes_step}
 
     # end to end through the public API with pinned host buffers
     e2e = None
@@ -503,11 +546,15 @@ def run_ours(args):
                          "peak": fp64_peak / 1e12 if fp64_peak else None,
                          "unit": "TFLOP/s",
                          "frac": achieved / fp64_peak if fp64_peak else None,
-                         "traffic": _traffic("k_sigmakin", f"{name}"),
+                         "traffic": _traffic("k_sigmakin", name, nevt / per_step)
+                         if per_step == 1 or args.precision == "fp64" else None,
                          "kernel": "k_sigmakin (FP64 pipe; peak = FP64 FMA probe, measured live)",
-                         "flops_per_launch": flops_launch},
+                         "flops_per_launch": flops_step / per_step,
+                         "launches_per_step": per_step,
+                         "ms_per_step": diag_ms / args.steps},
+            "roofline_colour_tc": roof_tc,
             "e2e": e2e,
-            "gpu_launches": args.steps,
+            "gpu_launches": n_launches,
             "clocks": clk,
             "cpu_baseline": cpu,
             "accuracy": accuracy,

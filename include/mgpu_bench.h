@@ -24,6 +24,19 @@ int mg_probe_fp64_peak(int blocks, int iters, int reps, double *flops_out);
 struct mg_process;
 int mg_debug_inject_stall(struct mg_process *p, unsigned int extra_bytes);
 
+/* Kernel timing of one process.  mg_set_kernel_timing(p, n) with n > 0
+ * creates n CUDA event pairs; every later mg_sigmakin or mg_sigmakin_hel
+ * call on p then records a pair on the caller's stream around each of its
+ * kernel launches.  n = 0 switches timing off and destroys the
+ * events.  mg_kernel_times waits for the last recorded event and writes per
+ * kind (0 diagram kernel k_sigmakin, 1 tensor-core colour sum, 2 per-event
+ * sum of the mixed path) the summed device milliseconds ms_out[3] and the
+ * launch counts launches_out[3] since the last reset; reset != 0 starts
+ * over.  More than n launches between resets: MG_ERR_UNSUPPORTED (nothing
+ * is reported).  Not thread-safe per process, like the other calls. */
+int mg_set_kernel_timing(struct mg_process *p, int max_launches);
+int mg_kernel_times(struct mg_process *p, int reset, double *ms_out, int *launches_out);
+
 /* Copies an internal buffer of the surrogate's last forward/backward pass to
  * the host as FP32 out[rows][cols] (padded widths): which = 0 activations of
  * layer input `layer` (0 = features), 1 pre-activations, 2 FP32 output

@@ -81,6 +81,8 @@ _SIGS = {
     "mg_batch_config": ([_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "mg_batch_destroy": ([_VP], None),
     "mg_sigmakin_batch": ([ctypes.c_int, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_VP), _VP], ctypes.c_int),
+    "mg_set_kernel_timing": ([_VP, ctypes.c_int], ctypes.c_int),
+    "mg_kernel_times": ([_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "mg_probe_fp64_peak": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
 }
 
@@ -166,6 +168,18 @@ class Process:
     def device_status(self, stream=None) -> int:
         """MG_OK or the status of the device-side work issued so far (syncs)."""
         return lib().mg_device_status(self._h, _stream(stream))
+
+    def set_kernel_timing(self, max_launches: int):
+        """Record CUDA events around each later kernel launch (0 = off)."""
+        _check(lib().mg_set_kernel_timing(self._h, max_launches), "mg_set_kernel_timing")
+
+    def kernel_times(self, reset=True):
+        """{kind: (device ms summed, launches)} since the last reset for the
+        kinds 'diagram', 'colour_tc', 'event_sum' (waits for the events)."""
+        ms = (ctypes.c_double * 3)()
+        n = (ctypes.c_int * 3)()
+        _check(lib().mg_kernel_times(self._h, int(reset), ms, n), "mg_kernel_times")
+        return {k: (ms[i], n[i]) for i, k in enumerate(("diagram", "colour_tc", "event_sum"))}
 
     def sigmakin_ex(self, momenta, out=None, alphas=None, channel=-1, sde=None, flow=None,
                     rnd_hel=None, hel_out=None, rnd_col=None, col_out=None, stream=None):

@@ -89,6 +89,9 @@ void free_proc(mg_process *p) {
     cudaFree(p->d_err);
     cudaFree(p->d_sel_hel);
     cudaFree(p->d_sel_jw);
+    for (int i = 0; i < 2 * p->tcap; i++) cudaEventDestroy(p->tev[i]);
+    free(p->tev);
+    free(p->tkind);
     free(p);
 }
 
@@ -392,8 +395,8 @@ static int sigmakin_mixed(mg_process *p, const double *mom, int64_t nevt, double
     if (chunk < ev_align) chunk = ev_align;
     if (chunk > nevt) chunk = (nevt + ev_align - 1) / ev_align * ev_align;
     const long long rows = (chunk * cpe + 127) / 128 * 128;
-    const int per_event = cpe >= 128 ? cpe / 128 : 1;
-    const long long parts = rows / 128 * (cpe >= 128 ? 1 : 128 / cpe);
+    const int per_event = mg_tc_parts_per_event(cpe);
+    const long long parts = rows / 128 * mg_tc_parts_per_tile(cpe);
     if (rows > p->jbuf_rows) {
         cudaFree(p->d_jbuf);
         p->d_jbuf = nullptr;
@@ -419,11 +422,17 @@ static int sigmakin_mixed(mg_process *p, const double *mom, int64_t nevt, double
     for (long long e0 = 0; e0 < nevt; e0 += chunk) {
         const long long n = (nevt - e0 < chunk) ? nevt - e0 : chunk;
         const long long used = (n * cpe + 127) / 128 * 128;
+        int slot = mg_timer_begin(p, s, MG_KT_DIAGRAM);
         MG_CUDA(mg_launch_sigmakin(dp, mom + e0 * p->tab->npar * 4, n, p->d_units, p->nunits, tpe,
                                    p->block, nullptr, nullptr, s, p->d_jbuf, p->kp, nup));
+        mg_timer_end(p, s, slot);
+        slot = mg_timer_begin(p, s, MG_KT_COLOUR_TC);
         MG_CUDA(mg_launch_colorsum_tc(p->d_jbuf, used, p->kp, p->d_cmat, p->np, p->tab->ncolor,
                                       cpe, p->debug_extra_tx, p->d_part, p->d_err, s));
+        mg_timer_end(p, s, slot);
+        slot = mg_timer_begin(p, s, MG_KT_EVENT_SUM);
         MG_CUDA(mg_launch_event_sum(p->d_part, n, per_event, p->factor, me + e0, s));
+        mg_timer_end(p, s, slot);
     }
     return MG_OK;
 }
@@ -452,8 +461,10 @@ static int sigmakin_impl(mg_process *p, const double *mom, int64_t nevt, double 
         if (me_hel) return MG_ERR_UNSUPPORTED;
         return sigmakin_mixed(p, mom, nevt, me, tpe, s);
     }
+    const int slot = mg_timer_begin(p, s, MG_KT_DIAGRAM);
     MG_CUDA(mg_launch_sigmakin(dev_view(p), mom, nevt, p->d_units, p->nunits, tpe, p->block, me,
                                me_hel, s));
+    mg_timer_end(p, s, slot);
     return MG_OK;
 }
 
@@ -470,7 +481,68 @@ int mg_sigmakin_hel(mg_process *p, const double *mom, int64_t nevt, double *me, 
     return sigmakin_impl(p, mom, nevt, me, me_hel, stream);
 }
 
+int mg_set_kernel_timing(mg_process *p, int max_launches) {
+    if (!p || max_launches < 0) return MG_ERR_BAD_ARG;
+    for (int i = 0; i < 2 * p->tcap; i++) cudaEventDestroy(p->tev[i]);
+    free(p->tev);
+    free(p->tkind);
+    p->tev = nullptr;
+    p->tkind = nullptr;
+    p->tcap = p->tn = p->tdropped = 0;
+    p->timing = 0;
+    if (max_launches == 0) return MG_OK;
+    p->tev = static_cast<cudaEvent_t *>(calloc(2 * (size_t)max_launches, sizeof(cudaEvent_t)));
+    p->tkind = static_cast<int *>(calloc((size_t)max_launches, sizeof(int)));
+    if (!p->tev || !p->tkind) return MG_ERR_NO_MEMORY;
+    for (int i = 0; i < 2 * max_launches; i++) {
+        cudaError_t e = cudaEventCreate(&p->tev[i]);
+        if (e != cudaSuccess) {
+            p->tcap = i / 2;   // pairs fully created so far are destroyed later
+            for (int j = 2 * p->tcap; j < i; j++) cudaEventDestroy(p->tev[j]);
+            return cuda_fail(e);
+        }
+    }
+    p->tcap = max_launches;
+    p->timing = 1;
+    return MG_OK;
+}
+
+int mg_kernel_times(mg_process *p, int reset, double *ms_out, int *launches_out) {
+    if (!p || !ms_out || !launches_out) return MG_ERR_BAD_ARG;
+    for (int k = 0; k < MG_KT_NKIND; k++) {
+        ms_out[k] = 0.0;
+        launches_out[k] = 0;
+    }
+    if (p->tdropped) return MG_ERR_UNSUPPORTED;
+    if (p->tn > 0) MG_CUDA(cudaEventSynchronize(p->tev[2 * p->tn - 1]));
+    for (int i = 0; i < p->tn; i++) {
+        float ms = 0.0f;
+        MG_CUDA(cudaEventElapsedTime(&ms, p->tev[2 * i], p->tev[2 * i + 1]));
+        ms_out[p->tkind[i]] += ms;
+        launches_out[p->tkind[i]] += 1;
+    }
+    if (reset) p->tn = 0;
+    return MG_OK;
+}
+
 }  // extern "C"
+
+int mg_timer_begin(mg_process *p, cudaStream_t s, int kind) {
+    if (!p->timing) return -1;
+    if (p->tn >= p->tcap) {
+        p->tdropped = 1;
+        return -1;
+    }
+    const int slot = p->tn++;
+    p->tkind[slot] = kind;
+    if (cudaEventRecord(p->tev[2 * slot], s) != cudaSuccess) p->tdropped = 1;
+    return slot;
+}
+
+void mg_timer_end(mg_process *p, cudaStream_t s, int slot) {
+    if (slot < 0) return;
+    if (cudaEventRecord(p->tev[2 * slot + 1], s) != cudaSuccess) p->tdropped = 1;
+}
 
 // ---------------------------------------------------------------------------
 // Helicity filter without device allocations.

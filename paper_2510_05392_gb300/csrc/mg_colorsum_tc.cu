@@ -12,16 +12,17 @@
 // One CTA computes Z = V C_hat^T for 128 columns (M = 128, N = NP colours,
 // K = KP per piece) with FP32 accumulation in tensor memory:
 //   Z = sum_{s in hi,mid,lo} V_s C_hi  +  sum_{s in hi,mid} V_s C_lo
-// (V_lo C_lo, relatively ~2^-24, is dropped), then each of the 128 epilogue
-// threads reads its row of Z from TMEM and forms sum_n V[m][n] Z[m][n] in
-// FP64 (V = hi + mid + lo from the same buffer).  Column sums are reduced per
-// event group in shared memory (fixed order) and written to part[].
+// (V_lo C_lo, relatively ~2^-24, is dropped), then the epilogue threads read
+// Z from TMEM and form sum_n V[m][n] Z[m][n] (compensated FP32, V = hi + mid
+// + lo from the operand tiles already in shared memory).  Partial sums go to
+// part[] in a fixed layout; k_event_sum adds each event's partials in order.
 //
 // Operands reach shared memory by TMA (cp.async.bulk.tensor, 128-byte
 // swizzle, box 64 x rows); one elected thread issues tcgen05.mma and
-// tcgen05.commit; every wait on an mbarrier is bounded: on timeout the CTA
-// records MG_TC_ERR_TIMEOUT in *err, waits (bounded) for its copies, frees its
-// tensor memory and returns.
+// tcgen05.commit; every wait on an mbarrier is bounded (about a second): on
+// timeout the warp records MG_TC_ERR_TIMEOUT in *err and a CTA-wide flag that
+// stops the other roles at their next wait, and the CTA frees its tensor
+// memory and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -125,27 +126,43 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *r) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Warp-specialised persistent kernel (192 threads):
+// Warp-specialised persistent kernel (2 + 8 TC_NSPLIT warps):
 //   warp 0  TMA producer: the two colour-matrix halves once, then the A chunks
 //           (one split x 64 colours x 128 rows, 16 KiB) of every tile through
 //           a ring of TC_STAGES shared-memory stages (full/empty mbarriers);
 //   warp 1  MMA issuer (one thread): per chunk 4 (hi) or 8 (hi + lo colour
-//           matrix) tcgen05.mma, then tcgen05.commit to free the stage; per
-//           tile a commit to the accumulator's "full" barrier; two TMEM
-//           accumulators alternate so the next tile's MMAs overlap this
-//           tile's epilogue;
-//   warps 2-5 epilogue: each thread owns one row (TMEM lane 32 (warp % 4) +
-//           lane), reads its row of Z and forms sum_n V Z in compensated FP32
-//           (exact products, two-sum accumulation, ~48 significant bits),
-//           then the event groups are summed in shared memory in a fixed order.
-constexpr int TC_STAGES = 6;
-constexpr int TC_THREADS = 192;
+//           matrix) tcgen05.mma, then tcgen05.commit to the stage's "empty"
+//           barrier; per tile a commit to the accumulator's "full" barrier;
+//           two TMEM accumulators alternate between the CTA's tiles;
+//   warps 2.. epilogue, two groups: group a takes the CTA's tiles i with
+//           i % 2 = a and TMEM accumulator a, so one group reads the next
+//           tile's operands (and frees their stages) while the other forms
+//           its sums.  In a group each thread owns one row (TMEM lane
+//           32 (warp % 4) + lane) and one of TC_NSPLIT colour sets, the
+//           16-colour groups g with g % TC_NSPLIT equal to its set.  A thread
+//           reads its row's colours from every A chunk in the stage the MMAs
+//           read (128-byte swizzle: 16-byte piece j of row m sits at piece
+//           j ^ (m % 8), so a warp's reads are conflict-free) and sums
+//           V = hi + mid + lo in registers; a stage is free once the MMA
+//           commit and the 4 TC_NSPLIT warps of the tile's group have
+//           arrived.  After the accumulator lands the thread forms its part of
+//           sum_n V Z in compensated FP32 (exact products, two-sum
+//           accumulation, ~48 significant bits), sums it in FP64 over the
+//           lanes of its event group (butterfly, fixed order) and writes one
+//           partial per warp segment to part[]; no two epilogue warps wait
+//           for each other.
+// The jamp rows are read from HBM exactly once (by TMA).
+constexpr int TC_STAGES = 8;   // deeper rings (10, 12) measured no faster
+constexpr int TC_NSPLIT = 2;                  // colour sets per row
+constexpr int TC_NGROUP = 2;                  // epilogue groups, one per TMEM accumulator
+constexpr int TC_GROUP_WARPS = 4 * TC_NSPLIT;
+constexpr int TC_EPI_WARPS = TC_NGROUP * TC_GROUP_WARPS;
+constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;
 
 struct TcSmem {
     uint64_t *bB, *full, *empty, *tfull, *tempty;
     uint32_t *tmem_slot;
     int *failed;
-    double *colsum;
 };
 
 __device__ __forceinline__ void tc_fail(int *failed, int *err) {
@@ -153,16 +170,18 @@ __device__ __forceinline__ void tc_fail(int *failed, int *err) {
     atomicExch(err, MG_TC_ERR_TIMEOUT);
 }
 
+// KCN = kp / 64 colour chunks per split (1 for up to 64 colours, 2 for up to 128).
+template <int KCN>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_colorsum_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                  const __nv_bfloat16 *__restrict__ jbuf, int kp, int np, int np_pad, int ncolor,
-                  int cpe, long long ntiles, int tmem_cols, uint32_t extra_tx,
+                  int np, int np_pad, int cpe, long long ntiles, int tmem_cols, uint32_t extra_tx,
                   double *__restrict__ part, int *__restrict__ err) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const int kc_n = kp / TC_KCHUNK;
-    const int nchunk = 3 * kc_n;                // A chunks per tile: split-major
+    constexpr int kc_n = KCN;
+    constexpr int kp = KCN * TC_KCHUNK;
+    constexpr int nchunk = 3 * KCN;             // A chunks per tile: split-major
     const int a_chunk = TC_M * 128;
     const int b_chunk = np * 128;
     unsigned char *sB = smem;                   // [2][kc_n] chunks, resident
@@ -176,7 +195,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     S.tempty = S.tfull + 2;
     S.tmem_slot = reinterpret_cast<uint32_t *>(S.tempty + 2);
     S.failed = reinterpret_cast<int *>(S.tmem_slot + 1);
-    S.colsum = reinterpret_cast<double *>(S.tmem_slot + 2);
+
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (warp == 0) {
@@ -190,11 +209,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         mbar_init(S.bB, 1);
         for (int i = 0; i < TC_STAGES; i++) {
             mbar_init(&S.full[i], 1);
-            mbar_init(&S.empty[i], 1);
+            mbar_init(&S.empty[i], 1 + TC_GROUP_WARPS);   // MMA commit + the tile's epilogue group
         }
         for (int i = 0; i < 2; i++) {
             mbar_init(&S.tfull[i], 1);
-            mbar_init(&S.tempty[i], 4);   // one arrival per epilogue warp
+            mbar_init(&S.tempty[i], TC_GROUP_WARPS);   // one arrival per warp of the group
         }
         *S.failed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -278,36 +297,85 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     } else {  // ------------------------------------------------ epilogue
         const int quarter = warp & 3;
+        const int grp = (warp - 2) / TC_GROUP_WARPS;              // tiles i with i % 2 == grp
+        const int split = ((warp - 2) % TC_GROUP_WARPS) >> 2;     // colour groups g % TC_NSPLIT
         const int m = quarter * 32 + lane;      // tile row this thread owns
-        const int et = tid - 64;                // 0..127 among epilogue threads
-        int acc = 0;
+        const int acc = grp;                    // the group's TMEM accumulator
         uint32_t aphase = 0;
-        const int gsize = cpe < TC_M ? cpe : TC_M;
-        const int ngroups = TC_M / gsize;
-        for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-            const bool landed =
-                __all_sync(0xffffffffu, !*(volatile int *)S.failed &&
-                                            mbar_wait(&S.tfull[acc], aphase, TC_WAIT_CYCLES));
-            if (!landed) {
+        const int gsize = cpe < TC_M ? cpe : TC_M;   // rows of one event in a tile (power of two)
+        const int wseg = gsize < 32 ? gsize : 32;    // lanes per warp segment
+        const int spg = gsize / wseg;                // segments per event group
+        const int ppt = TC_NSPLIT * (TC_M / wseg);   // partials per tile
+        // partial of (tile t, group m / gsize, colour set, segment in group)
+        const long long pidx0 = (long long)((m / gsize) * TC_NSPLIT + split) * spg + (m % gsize) / wseg;
+        bool ok = true;
+        long long i = grp;                      // index of the tile among this CTA's tiles
+        for (long long t = blockIdx.x + grp * (long long)gridDim.x; ok && t < ntiles;
+             t += TC_NGROUP * (long long)gridDim.x, i += TC_NGROUP) {
+            float v[kp / TC_NSPLIT];            // v[16 (g / TC_NSPLIT) + j] = V of colour 16 g + j
+#pragma unroll
+            for (int c = 0; c < nchunk; c++) {
+                const long long gch = i * nchunk + c;   // chunk's place in the CTA's sequence
+                const int stage = (int)(gch % TC_STAGES);
+                const uint32_t phase = (uint32_t)((gch / TC_STAGES) & 1);
+                if (ok)
+                    ok = __all_sync(0xffffffffu, !*(volatile int *)S.failed &&
+                                                     mbar_wait(&S.full[stage], phase, TC_WAIT_CYCLES));
+                if (ok) {
+                    const unsigned char *rowp = sA + stage * a_chunk + m * 128;
+                    const int sp = c / kc_n, kc = c % kc_n;
+#pragma unroll
+                    for (int gg = 0; gg < 4 / TC_NSPLIT; gg++) {   // groups 4 kc + split + TC_NSPLIT gg
+#pragma unroll
+                        for (int pc = 0; pc < 2; pc++) {    // 8-colour pieces of the group
+                            const int j = 2 * (split + TC_NSPLIT * gg) + pc;
+                            const uint4 q =
+                                *reinterpret_cast<const uint4 *>(rowp + ((j ^ (m & 7)) << 4));
+                            const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+                            float *d = &v[(kc * (4 / TC_NSPLIT) + gg) * 16 + 8 * pc];
+#pragma unroll
+                            for (int i = 0; i < 4; i++) {
+                                const float lo = __uint_as_float(w[i] << 16);
+                                const float hi = __uint_as_float(w[i] & 0xFFFF0000u);
+                                if (sp == 0) {
+                                    d[2 * i] = lo;
+                                    d[2 * i + 1] = hi;
+                                } else {
+                                    d[2 * i] += lo;
+                                    d[2 * i + 1] += hi;
+                                }
+                            }
+                        }
+                    }
+                    __syncwarp();
+                    if (lane == 0)
+                        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(
+                                         smem_u32(&S.empty[stage]))
+                                     : "memory");
+                }
+            }
+            if (ok)
+                ok = __all_sync(0xffffffffu, !*(volatile int *)S.failed &&
+                                                 mbar_wait(&S.tfull[acc], aphase, TC_WAIT_CYCLES));
+            if (!ok) {
                 if (lane == 0) tc_fail(S.failed, err);
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const __nv_bfloat16 *row = jbuf + (t * TC_M + m) * (long long)(3 * kp);
             const uint32_t taddr = tmem + (uint32_t)(acc * np_pad) + ((uint32_t)(quarter * 32) << 16);
             float sh = 0.0f, sl = 0.0f;
-            for (int c0 = 0; c0 < np; c0 += 16) {
-                uint32_t z[16];
-                tmem_ld16(taddr + (uint32_t)c0, z);
 #pragma unroll
-                for (int j = 0; j < 16; j++) {
-                    const int n = c0 + j;
-                    if (n < ncolor) {
-                        const float v = __bfloat162float(row[n]) + __bfloat162float(row[kp + n]) +
-                                        __bfloat162float(row[2 * kp + n]);
+            for (int gl = 0; gl < kp / (16 * TC_NSPLIT); gl++) {
+                const int c0 = 16 * (TC_NSPLIT * gl + split);
+                if (c0 < np) {   // colours >= np: zero columns of C_hat, Z = 0
+                    uint32_t z[16];
+                    tmem_ld16(taddr + (uint32_t)c0, z);
+#pragma unroll
+                    for (int j = 0; j < 16; j++) {
+                        const float vv = v[16 * gl + j];
                         const float zz = __uint_as_float(z[j]);
-                        const float p = v * zz;
-                        const float pe = fmaf(v, zz, -p);       // exact product p + pe
+                        const float p = vv * zz;
+                        const float pe = fmaf(vv, zz, -p);      // exact product p + pe
                         const float s = sh + p;                  // two-sum (sh, p)
                         const float bp = s - sh;
                         const float se = (sh - (s - bp)) + (p - bp);
@@ -318,19 +386,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
-            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&S.tempty[acc])) : "memory");
-            S.colsum[m] = (double)sh + (double)sl;
-            asm volatile("bar.sync 1, 128;" ::: "memory");
-            if (et < ngroups) {
-                double sum = 0.0;
-                for (int j = 0; j < gsize; j++) sum += S.colsum[et * gsize + j];
-                part[t * ngroups + et] = sum;
-            }
-            asm volatile("bar.sync 1, 128;" ::: "memory");
-            if (++acc == 2) {
-                acc = 0;
-                aphase ^= 1;
-            }
+            if (lane == 0)
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&S.tempty[acc]))
+                             : "memory");
+            // butterfly over the warp segment (every lane ends with the same bits)
+            double cs = (double)sh + (double)sl;
+            for (int off = wseg >> 1; off >= 1; off >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, off);
+            if ((lane & (wseg - 1)) == 0) part[t * ppt + pidx0] = cs;
+            aphase ^= 1;
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -343,7 +406,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
 }
 
-// me[e] = factor * (sum of the event's partial column sums), fixed order.
+// me[e] = factor * (sum of the event's partial sums), fixed order: the
+// partials of one event are contiguous (tile, event group, colour set,
+// segment), per_event of them.
 __global__ void k_event_sum(const double *__restrict__ part, long long nevt, int per_event,
                             double factor, double *__restrict__ me) {
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -386,16 +451,28 @@ bool make_map(CUtensorMap *m, const void *base, uint64_t rows, uint64_t cols, ui
 
 }  // namespace
 
+int mg_tc_parts_per_tile(int cpe) {
+    const int gsize = cpe < TC_M ? cpe : TC_M;
+    return TC_NSPLIT * (TC_M / (gsize < 32 ? gsize : 32));
+}
+
+int mg_tc_parts_per_event(int cpe) {
+    const int gsize = cpe < TC_M ? cpe : TC_M;
+    const int tiles = cpe > TC_M ? cpe / TC_M : 1;
+    return tiles * TC_NSPLIT * (gsize / (gsize < 32 ? gsize : 32));
+}
+
 size_t mg_tc_smem_bytes(int kp, int np) {
     const int kc_n = kp / TC_KCHUNK;
     return 1024 + (size_t)2 * kc_n * np * 128 + (size_t)TC_STAGES * TC_M * 128 +
-           (1 + 2 * TC_STAGES + 4) * 8 + 16 + TC_M * 8;
+           (1 + 2 * TC_STAGES + 4) * 8 + 16;
 }
 
 cudaError_t mg_launch_colorsum_tc(const __nv_bfloat16 *jbuf, long long ncols_alloc, int kp,
                                   const __nv_bfloat16 *cmat, int np, int ncolor, int cpe,
                                   uint32_t extra_tx, double *part, int *err, cudaStream_t stream) {
-    if (ncols_alloc % TC_M || kp % TC_KCHUNK || np % 16 || np > 128 || kp > 256)
+    if (ncols_alloc % TC_M || kp % TC_KCHUNK || np % 16 || np > 128 || kp > 2 * TC_KCHUNK ||
+        np > kp || cpe < 8 || (cpe & (cpe - 1)))
         return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
     if (!make_map(&ma, jbuf, (uint64_t)ncols_alloc, (uint64_t)3 * kp, TC_M)) return cudaErrorInvalidValue;
@@ -404,16 +481,22 @@ cudaError_t mg_launch_colorsum_tc(const __nv_bfloat16 *jbuf, long long ncols_all
     while (np_pad < np) np_pad <<= 1;
     const int tmem_cols = 2 * np_pad;  // two accumulators
     const size_t smem = mg_tc_smem_bytes(kp, np);
-    cudaError_t e = cudaFuncSetAttribute(k_colorsum_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_colorsum_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_colorsum_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, nsm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     const long long ntiles = ncols_alloc / TC_M;
     const long long grid = ntiles < nsm ? ntiles : nsm;   // persistent: one CTA per SM
-    k_colorsum_tc<<<(unsigned)grid, TC_THREADS, smem, stream>>>(ma, mb, jbuf, kp, np, np_pad, ncolor,
-                                                                cpe, ntiles, tmem_cols, extra_tx, part, err);
+    if (kp == TC_KCHUNK)
+        k_colorsum_tc<1><<<(unsigned)grid, TC_THREADS, smem, stream>>>(ma, mb, np, np_pad, cpe, ntiles,
+                                                                       tmem_cols, extra_tx, part, err);
+    else
+        k_colorsum_tc<2><<<(unsigned)grid, TC_THREADS, smem, stream>>>(ma, mb, np, np_pad, cpe, ntiles,
+                                                                       tmem_cols, extra_tx, part, err);
     return cudaGetLastError();
 }
 

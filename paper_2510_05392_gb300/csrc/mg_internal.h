@@ -106,14 +106,18 @@ cudaError_t mg_launch_select(const double *me_hel, int nhel, const double *jw, i
 cudaError_t mg_launch_helmask(const double *me_hel, int64_t n, int nhel, double rel,
                               unsigned char *mask, cudaStream_t stream);
 // tensor-core colour sum over ncols_alloc (multiple of 128) GEMM rows of jbuf
-// ([ncols][3*kp] BF16) with cmat ([2*np][kp] BF16: D*C split hi/lo); writes
-// one partial sum per event group of cpe rows (per 128-row tile if cpe >= 128)
+// ([ncols][3*kp] BF16) with cmat ([2*np][kp] BF16: D*C split hi/lo), cpe
+// rows per event (a power of two >= 8); writes mg_tc_parts_per_tile(cpe)
+// partial sums per 128-row tile, mg_tc_parts_per_event(cpe) per event,
+// contiguous per event
 cudaError_t mg_launch_colorsum_tc(const __nv_bfloat16 *jbuf, long long ncols_alloc, int kp,
                                   const __nv_bfloat16 *cmat, int np, int ncolor, int cpe,
                                   uint32_t extra_tx, double *part, int *err, cudaStream_t stream);
 cudaError_t mg_launch_event_sum(const double *part, long long nevt, int per_event, double factor,
                                 double *me, cudaStream_t stream);
 size_t mg_tc_smem_bytes(int kp, int np);
+int mg_tc_parts_per_tile(int cpe);
+int mg_tc_parts_per_event(int cpe);
 // persistent multi-process kernel: counter reset + one launch of grid CTAs
 cudaError_t mg_launch_batch(const mg_batch_item *d_items, int nitems, unsigned long long *d_counter,
                             long long total_slots, int grid, cudaStream_t stream);

@@ -34,7 +34,20 @@ struct mg_process {
     double *d_sel_hel;           // [cap][2^npar] per-helicity |M_h|^2
     double *d_sel_jw;            // [cap][ncolor] helicity-summed |J_s|^2
     long long sel_cap;
+    // kernel timing (measurement hook): CUDA event pairs around each launch
+    int timing;                  // 1 while enabled
+    cudaEvent_t *tev;            // [2 * tcap]
+    int *tkind;                  // [tcap] MG_KT_* of each recorded launch
+    int tcap, tn, tdropped;
 };
+
+// kinds of timed launches
+enum { MG_KT_DIAGRAM = 0, MG_KT_COLOUR_TC = 1, MG_KT_EVENT_SUM = 2, MG_KT_NKIND = 3 };
+
+// Timing of one launch: mg_timer_begin records the start event (returns the
+// slot, or -1 when timing is off or the pool is full), mg_timer_end the stop.
+int mg_timer_begin(mg_process *p, cudaStream_t s, int kind);
+void mg_timer_end(mg_process *p, cudaStream_t s, int slot);
 
 // helpers of mg_api.cu used by the other host files
 int mg_check_dev_ptr(const void *ptr, int device);

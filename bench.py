@@ -358,6 +358,7 @@ def run_surrogate(args):
     wt = torch.zeros(ncand, dtype=torch.float64, device=dev)
     nex = ctypes.c_int64()
     torch.cuda.synchronize(dev)
+    launches0 = binding.launch_count()
     t0 = time.perf_counter()
     rc = L.mg_unweight2(p.handle, h, ctypes.c_void_p(cad.data_ptr()), ctypes.c_void_p(phd.data_ptr()),
                         ctypes.c_void_p(u1d.data_ptr()), ctypes.c_void_p(u2d.data_ptr()), ncand, what_max,
@@ -365,6 +366,7 @@ def run_surrogate(args):
                         ctypes.byref(nex), sp)
     torch.cuda.synchronize(dev)
     t_two = time.perf_counter() - t0
+    launches_two = binding.launch_count() - launches0
     assert rc == 0, rc
     wts = wt.cpu().numpy()
     nacc = int((acc.cpu().numpy() != 0).sum())
@@ -391,7 +393,7 @@ def run_surrogate(args):
         "plain_hit_or_miss": {"efficiency": eff_plain, "w_max_quantile": w_q,
                               "unweighted_events_per_s": plain_unw_per_s},
         "surrogate_gain_unweighted_events_per_s": two_unw_per_s / plain_unw_per_s,
-        "gpu_launches": None,
+        "gpu_launches": launches_two,
     }
     print(json.dumps(line), flush=True)
     L.mg_sur_destroy(h)
@@ -444,6 +446,7 @@ def run_ours(args):
     # per-kernel CUDA events on the launching stream, recorded by the library
     p.set_kernel_timing(args.steps * 3 * 256)
     p.kernel_times(reset=True)
+    launches0 = binding.launch_count()
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
@@ -458,6 +461,7 @@ def run_ours(args):
     if ws > 1:
         torch.distributed.barrier()
     clk = clocks.stop() if clocks else None
+    launches_lib = binding.launch_count() - launches0
     kt = p.kernel_times(reset=True)
     p.set_kernel_timing(0)
     launch_ms = [a.elapsed_time(b) for a, b in ev]
@@ -465,6 +469,7 @@ def run_ours(args):
     value = ws * nevt * args.steps / t_dev
     ms_step = 1e3 * t_dev / args.steps
     n_launches = sum(n for _, n in kt.values())
+    assert n_launches == launches_lib, (n_launches, launches_lib)
 
     # algorithmic FP64 work of the diagram kernel per step (mixed: the colour
     # sum runs on the tensor cores, so only the diagram work is FP64), over

@@ -37,6 +37,11 @@ int mg_debug_inject_stall(struct mg_process *p, unsigned int extra_bytes);
 int mg_set_kernel_timing(struct mg_process *p, int max_launches);
 int mg_kernel_times(struct mg_process *p, int reset, double *ms_out, int *launches_out);
 
+/* Number of kernel launches the library has issued since it was loaded
+ * (every process and stream; the FP64 peak probe and replays of captured CUDA
+ * graphs not included).  For counting the launches of a timed region. */
+int mg_launch_count(unsigned long long *out);
+
 /* Copies an internal buffer of the surrogate's last forward/backward pass to
  * the host as FP32 out[rows][cols] (padded widths): which = 0 activations of
  * layer input `layer` (0 = features), 1 pre-activations, 2 FP32 output

@@ -83,6 +83,7 @@ _SIGS = {
     "mg_sigmakin_batch": ([ctypes.c_int, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_VP), _VP], ctypes.c_int),
     "mg_set_kernel_timing": ([_VP, ctypes.c_int], ctypes.c_int),
     "mg_kernel_times": ([_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "mg_launch_count": ([ctypes.POINTER(ctypes.c_ulonglong)], ctypes.c_int),
     "mg_probe_fp64_peak": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
 }
 
@@ -207,6 +208,14 @@ class Process:
         _check(lib().mg_helicity_mask(self._h, m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))),
                "mg_helicity_mask")
         return m
+
+
+def launch_count() -> int:
+    """Kernel launches the library has issued so far (graph replays and the
+    FP64 peak probe not included)."""
+    n = ctypes.c_ulonglong(0)
+    _check(lib().mg_launch_count(ctypes.byref(n)), "mg_launch_count")
+    return n.value
 
 
 class Batch:

@@ -8,6 +8,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
 #include <mutex>
 #include <string>
 
@@ -526,6 +527,16 @@ int mg_kernel_times(mg_process *p, int reset, double *ms_out, int *launches_out)
 }
 
 }  // extern "C"
+
+static std::atomic<unsigned long long> g_launches{0};
+
+void mg_note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+extern "C" int mg_launch_count(unsigned long long *out) {
+    if (!out) return MG_ERR_BAD_ARG;
+    *out = g_launches.load(std::memory_order_relaxed);
+    return MG_OK;
+}
 
 int mg_timer_begin(mg_process *p, cudaStream_t s, int kind) {
     if (!p->timing) return -1;

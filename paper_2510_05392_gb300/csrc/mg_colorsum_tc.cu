@@ -491,6 +491,7 @@ cudaError_t mg_launch_colorsum_tc(const __nv_bfloat16 *jbuf, long long ncols_all
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     const long long ntiles = ncols_alloc / TC_M;
     const long long grid = ntiles < nsm ? ntiles : nsm;   // persistent: one CTA per SM
+    mg_note_launch();
     if (kp == TC_KCHUNK)
         k_colorsum_tc<1><<<(unsigned)grid, TC_THREADS, smem, stream>>>(ma, mb, np, np_pad, cpe, ntiles,
                                                                        tmem_cols, extra_tx, part, err);
@@ -503,6 +504,7 @@ cudaError_t mg_launch_colorsum_tc(const __nv_bfloat16 *jbuf, long long ncols_all
 cudaError_t mg_launch_event_sum(const double *part, long long nevt, int per_event, double factor,
                                 double *me, cudaStream_t stream) {
     if (nevt <= 0) return cudaSuccess;
+    mg_note_launch();
     k_event_sum<<<(unsigned)((nevt + 255) / 256), 256, 0, stream>>>(part, nevt, per_event, factor, me);
     return cudaGetLastError();
 }

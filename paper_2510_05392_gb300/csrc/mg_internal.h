@@ -116,6 +116,9 @@ cudaError_t mg_launch_colorsum_tc(const __nv_bfloat16 *jbuf, long long ncols_all
 cudaError_t mg_launch_event_sum(const double *part, long long nevt, int per_event, double factor,
                                 double *me, cudaStream_t stream);
 size_t mg_tc_smem_bytes(int kp, int np);
+// counts a kernel launch of the library (measurement; replays of captured
+// graphs are not launches of this kind and are not counted)
+void mg_note_launch();
 int mg_tc_parts_per_tile(int cpe);
 int mg_tc_parts_per_event(int cpe);
 // persistent multi-process kernel: counter reset + one launch of grid CTAs

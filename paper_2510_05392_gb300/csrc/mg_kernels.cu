@@ -507,6 +507,7 @@ cudaError_t mg_launch_sigmakin(const mg_dev_proc &dp, const double *mom, int64_t
     const long long threads = (long long)nevt * tpe;
     const long long grid = (threads + block - 1) / block;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
+    mg_note_launch();
     switch (dp.table_index) {
 #define MG_LAUNCH(IDX, NG, NSG, NSF, NSA, NC)                                                    \
     case IDX:                                                                                    \
@@ -529,6 +530,7 @@ cudaError_t mg_launch_sigmakin(const mg_dev_proc &dp, const double *mom, int64_t
 
 cudaError_t mg_launch_helmask(const double *me_hel, int64_t n, int nhel, double rel,
                               unsigned char *mask, cudaStream_t stream) {
+    mg_note_launch();
     k_helmask<<<(nhel + 127) / 128, 128, 0, stream>>>(me_hel, n, nhel, rel, mask);
     return cudaGetLastError();
 }
@@ -538,6 +540,7 @@ cudaError_t mg_launch_batch(const mg_batch_item *d_items, int nitems, unsigned l
     cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), stream);
     if (e != cudaSuccess) return e;
     if (total_slots <= 0) return cudaSuccess;
+    mg_note_launch();
     k_batch<<<grid, 128, 0, stream>>>(d_items, nitems, d_counter, total_slots);
     return cudaGetLastError();
 }
@@ -574,6 +577,7 @@ cudaError_t mg_launch_select(const double *me_hel, int nhel, const double *jw, i
                              long long nevt, const double *rh, const double *rc, int *hel_out,
                              int *col_out, cudaStream_t stream) {
     if (nevt <= 0) return cudaSuccess;
+    mg_note_launch();
     k_select<<<(unsigned)((nevt + 127) / 128), 128, 0, stream>>>(me_hel, nhel, jw, ncolor, nevt, rh, rc,
                                                                hel_out, col_out);
     return cudaGetLastError();

@@ -360,6 +360,7 @@ int forward(mg_surrogate *s, int M, cudaStream_t st) {
     for (int l = 0; l < s->nl; l++) {
         const int tiles = (M / WM) * (s->outp[l] / WM);
         const bool last = (l == s->nl - 1);
+        mg_note_launch();
         k_fwd<<<blocks_for(tiles, 4), 128, 0, st>>>(s->A[l], s->W16[l], s->b[l], M, s->outp[l],
                                                    s->in[l], last ? 0 : 1, s->Z[l],
                                                    last ? nullptr : s->A[l + 1]);
@@ -372,11 +373,14 @@ int forward(mg_surrogate *s, int M, cudaStream_t st) {
 int backward(mg_surrogate *s, int M, cudaStream_t st) {
     for (int l = s->nl - 1; l >= 0; l--) {
         const int tiles_w = (s->outp[l] / WM) * (s->in[l] / WM);
+        mg_note_launch();
         k_bwd_weight<<<blocks_for(tiles_w, 4), 128, 0, st>>>(s->dZ[l], s->A[l], M, s->outp[l],
                                                             s->in[l], s->gW[l]);
+        mg_note_launch();
         k_bias_grad<<<blocks_for(s->outp[l], 128), 128, 0, st>>>(s->dZ32[l], M, s->outp[l], s->gb[l]);
         if (l > 0) {
             const int tiles_d = (M / WM) * (s->in[l] / WM);
+            mg_note_launch();
             k_bwd_data<<<blocks_for(tiles_d, 4), 128, 0, st>>>(s->dZ[l], s->W16[l], s->Z[l - 1], M,
                                                               s->outp[l], s->in[l], s->dZ[l - 1],
                                                               s->dZ32[l - 1]);
@@ -524,6 +528,7 @@ int mg_sur_debug_buffer(mg_surrogate *s, int which, int layer, int rows, float *
 // mu, sigma of log|M|^2 over me_dev[n]
 int mg_sur_fit_target(mg_surrogate *s, const double *me, int64_t n, void *stream) {
     if (!s || !me || n < 2) return MG_ERR_BAD_ARG;
+    mg_note_launch();
     k_logstats<<<1, 256, 0, (cudaStream_t)stream>>>(me, n, s->ms);
     SCHECK(cudaGetLastError());
     return MG_OK;
@@ -541,10 +546,12 @@ int mg_sur_loss_grad(mg_surrogate *s, const double *mom, int npar, const float *
                      double *loss_out, void *stream) {
     if (!s || !mom || !y || m < 16 || m % 16 || m > s->bmax || npar < 2) return MG_ERR_BAD_ARG;
     cudaStream_t st = (cudaStream_t)stream;
+    mg_note_launch();
     k_features<<<blocks_for(m, 128), 128, 0, st>>>(mom, m, npar, s->in[0], s->A[0]);
     int rc = forward(s, m, st);
     if (rc) return rc;
     const int nb = blocks_for(m, 256);
+    mg_note_launch();
     k_loss<<<nb, 256, 0, st>>>(s->Z[s->nl - 1], m, s->outp[s->nl - 1], y, s->dZ[s->nl - 1],
                                s->dZ32[s->nl - 1], s->part);
     rc = backward(s, m, st);
@@ -568,8 +575,10 @@ int mg_sur_adam(mg_surrogate *s, double lr, void *stream) {
     const float c1 = 1.0f - powf(b1, (float)s->t), c2 = 1.0f - powf(b2, (float)s->t);
     for (int l = 0; l < s->nl; l++) {
         const long long nw = (long long)s->outp[l] * s->in[l];
+        mg_note_launch();
         k_adam<<<blocks_for(nw, 256), 256, 0, st>>>(s->W[l], s->mW[l], s->vW[l], s->gW[l], s->W16[l], nw,
                                                    (float)lr, b1, b2, 1e-8f, c1, c2);
+        mg_note_launch();
         k_adam<<<blocks_for(s->outp[l], 256), 256, 0, st>>>(s->b[l], s->mb[l], s->vb[l], s->gb[l], nullptr,
                                                            s->outp[l], (float)lr, b1, b2, 1e-8f, c1, c2);
     }
@@ -590,6 +599,7 @@ int mg_sur_train(mg_surrogate *s, const double *mom, int npar, const double *me,
         acc = 0.0;
         for (int64_t bi = 0; bi < nbatch; bi++) {
             const double *mb = mom + (size_t)bi * batch * npar * 4;
+            mg_note_launch();
             k_target<<<blocks_for(batch, 256), 256, 0, st>>>(me + bi * batch, batch, s->ms, s->y);
             double l = 0.0;
             int rc = mg_sur_loss_grad(s, mb, npar, s->y, batch, ep == epochs - 1 ? &l : nullptr, st);
@@ -611,11 +621,13 @@ int mg_sur_predict(mg_surrogate *s, const double *mom, int npar, int64_t n, doub
     for (int64_t e0 = 0; e0 < n; e0 += s->bmax) {
         const int64_t c = (n - e0 < s->bmax) ? n - e0 : s->bmax;
         const int M = (int)((c + WM - 1) / WM * WM);
+        mg_note_launch();
         k_features<<<blocks_for(c, 128), 128, 0, st>>>(mom + e0 * npar * 4, c, npar, s->in[0], s->A[0]);
         if (M > c)
             SCHECK(cudaMemsetAsync(s->A[0] + c * s->in[0], 0, (size_t)(M - c) * s->in[0] * 2, st));
         int rc = forward(s, M, st);
         if (rc) return rc;
+        mg_note_launch();
         k_pred<<<blocks_for(c, 256), 256, 0, st>>>(s->Z[s->nl - 1], s->outp[s->nl - 1], c, s->ms, logme + e0);
     }
     SCHECK(cudaGetLastError());
@@ -718,7 +730,9 @@ int mg_unweight2(mg_process *p, mg_surrogate *s, const double *mom, const double
     if (e != cudaSuccess) rc = sur_fail(e);
     if (!rc) rc = mg_sur_predict(s, mom, npar, n, logme, st);
     if (!rc) {
+        mg_note_launch();
         k_stage1<<<nb, 1024, 0, st>>>(logme, phi, u1, n, what_max, what, flag, bcount);
+        mg_note_launch();
         k_scan<<<1, 32, 0, st>>>(bcount, nb, total);
         e = cudaMemcpyAsync(&htotal, total, sizeof(long long), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -729,6 +743,7 @@ int mg_unweight2(mg_process *p, mg_surrogate *s, const double *mom, const double
         if (e == cudaSuccess) e = cudaMalloc(&me1, htotal * 8);
         if (e != cudaSuccess) rc = sur_fail(e);
         if (!rc) {
+            mg_note_launch();
             k_compact<<<nb, 1024, 0, st>>>(flag, bcount, n, mom, npar, idx, mom1);
             rc = mg_sigmakin(p, mom1, htotal, me1, st);
         }
@@ -737,9 +752,11 @@ int mg_unweight2(mg_process *p, mg_surrogate *s, const double *mom, const double
         e = cudaMemsetAsync(accept, 0, n, st);
         if (e == cudaSuccess) e = cudaMemsetAsync(weight, 0, n * 8, st);
         if (e != cudaSuccess) rc = sur_fail(e);
-        if (!rc && htotal > 0)
+        if (!rc && htotal > 0) {
+            mg_note_launch();
             k_stage2<<<blocks_for(htotal, 256), 256, 0, st>>>(idx, me1, htotal, phi, what, u2, what_max,
                                                              r_max, accept, weight);
+        }
         e = cudaStreamSynchronize(st);
         if (!rc && e != cudaSuccess) rc = sur_fail(e);
     }

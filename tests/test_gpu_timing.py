@@ -17,9 +17,12 @@ def test_kernel_times_count_every_launch(precision):
     p.filter_helicities(mom[:16])
     out = torch.empty(300, dtype=torch.float64, device="cuda")
     p.set_kernel_timing(64)
+    n0 = binding.launch_count()
     for _ in range(3):
         p.sigmakin(mom, out)
+    launched = binding.launch_count() - n0
     kt = p.kernel_times(reset=True)
+    assert launched == sum(n for _, n in kt.values())
     ms, n = kt["diagram"]
     assert n == 3 and ms > 0.0
     if precision == binding.MG_MIXED_BF16:

@@ -307,9 +307,18 @@ int oracle_me(int n, const double *mom, int64_t nevt, const double *par_in, cons
     int npar = n + 2, nhel = 1 << npar;
     params_t par = {par_in[0], par_in[1]};
     double g2n = pow(par_in[2], 2 * n);
-    double *C = (double *)malloc(sizeof(double) * ncolor * ncolor);
+    double *C = (double *)malloc(sizeof(double) * (size_t)ncolor * ncolor);
     if (!C) return -2;
-    for (int i = 0; i < ncolor * ncolor; i++) C[i] = (double)cnum[i] / (double)cden;
+    for (size_t i = 0; i < (size_t)ncolor * ncolor; i++) C[i] = (double)cnum[i] / (double)cden;
+    /* |M_h|^2 of every (event, helicity) pair first, in parallel over the
+     * pairs (a handful of events of the large processes still spreads over
+     * all threads), then each event's sum over h in order */
+    const int64_t npairs = nevt * (int64_t)nhel;
+    double *mh_all = (double *)malloc(sizeof(double) * (size_t)(npairs > 0 ? npairs : 1));
+    if (!mh_all) {
+        free(C);
+        return -2;
+    }
     int status = 0;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -326,33 +335,40 @@ int oracle_me(int n, const double *mom, int64_t nevt, const double *par_in, cons
 #ifdef _OPENMP
 #pragma omp for schedule(dynamic, 1)
 #endif
-        for (int64_t e = 0; e < nevt; e++) {
+        for (int64_t q = 0; q < npairs; q++) {
             if (!A) continue;
+            const int64_t e = q / nhel;
+            const int h = (int)(q % nhel);
             const double *p = mom + (size_t)e * npar * 4;
-            double tot = 0;
-            for (int h = 0; h < nhel; h++) {
-                double mh = 0;
-                if (!hel_mask || hel_mask[h]) {
-                    cplx eps[MAXG][4], ub[4], v[4];
-                    double kin[MAXG][4];
-                    externals(n, p, h, -1, eps, kin, ub, v);
-                    for (int s = 0; s < ncolor; s++)
-                        A[s] = bg_amplitude(n, perms + s * n, eps, kin, ub, v, p + 8, &par);
-                    double acc = 0;
-                    for (int s = 0; s < ncolor; s++) {
-                        cplx z = 0;
-                        for (int t = 0; t < ncolor; t++) z += C[s * ncolor + t] * A[t];
-                        acc += creal(conj(A[s]) * z);
-                    }
-                    mh = g2n * acc / iden;
+            double mh = 0;
+            if (!hel_mask || hel_mask[h]) {
+                cplx eps[MAXG][4], ub[4], v[4];
+                double kin[MAXG][4];
+                externals(n, p, h, -1, eps, kin, ub, v);
+                for (int s = 0; s < ncolor; s++)
+                    A[s] = bg_amplitude(n, perms + s * n, eps, kin, ub, v, p + 8, &par);
+                double acc = 0;
+                for (int s = 0; s < ncolor; s++) {
+                    cplx z = 0;
+                    for (int t = 0; t < ncolor; t++) z += C[(size_t)s * ncolor + t] * A[t];
+                    acc += creal(conj(A[s]) * z);
                 }
-                if (me_hel_out) me_hel_out[(size_t)e * nhel + h] = mh;
-                tot += mh;
+                mh = g2n * acc / iden;
             }
-            me_out[e] = tot;
+            mh_all[q] = mh;
         }
         free(A);
     }
+    for (int64_t e = 0; e < nevt; e++) {
+        double tot = 0;
+        for (int h = 0; h < nhel; h++) {
+            const double mh = mh_all[e * nhel + h];
+            if (me_hel_out) me_hel_out[(size_t)e * nhel + h] = mh;
+            tot += mh;
+        }
+        me_out[e] = tot;
+    }
+    free(mh_all);
     free(C);
     return status;
 }

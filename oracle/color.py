@@ -108,12 +108,58 @@ def gluon_orderings(n: int):
     return list(itertools.permutations(range(n)))
 
 
+def _lex_rank(P):
+    """Lexicographic rank of each row of P (permutations of range(n)), i.e.
+    its index in itertools.permutations order (Lehmer code)."""
+    import numpy as np
+    m, n = P.shape
+    rank = np.zeros(m, dtype=np.int64)
+    used = np.zeros((m, n), dtype=bool)
+    rows = np.arange(m)
+    for k in range(n):
+        smaller_unused = (~used) & (np.arange(n)[None, :] < P[:, k:k + 1])
+        rank = rank * (n - k) + smaller_unused.sum(axis=1)
+        used[rows, P[:, k]] = True
+    return rank
+
+
+def color_matrix_relabelled(n: int):
+    """The same matrix from n! traces instead of (n!)^2.
+
+    The gluon labels are summed dummies, so renaming them by the inverse of
+    ordering s leaves C_st unchanged and turns s into the identity:
+    C_st = C_(id, r) with r_k = (position of t_k in s).  Returns
+    (C_hat int64 array [n!][n!], D, perms).
+    """
+    import numpy as np
+    perms = gluon_orderings(n)
+    base = [trace_value(tuple(reversed(range(n))) + tuple(r)) for r in perms]
+    D = 1
+    for x in base:
+        D = D * x.denominator // math.gcd(D, x.denominator)
+    base_hat = np.array([int(x * D) for x in base], dtype=np.int64)
+    P = np.array(perms, dtype=np.int64)
+    m = len(perms)
+    Chat = np.empty((m, m), dtype=np.int64)
+    for s in range(m):
+        pos = np.empty(n, dtype=np.int64)
+        pos[P[s]] = np.arange(n)          # pos[a] = position of label a in s
+        Chat[s] = base_hat[_lex_rank(pos[P])]
+    return Chat, D, perms
+
+
 def color_matrix(n: int):
     """Exact colour matrix for n gluons.
 
-    Returns (C_hat, D, perms): C_hat list of lists of ints (n! x n!), D the
-    common denominator (C = C_hat / D), perms the orderings.
+    Returns (C_hat, D, perms): C_hat (n! x n! integers) with D the common
+    denominator (C = C_hat / D), perms the orderings.  Up to 6 gluons every
+    entry is its own trace (lists of ints); beyond that the (n!)^2 traces are
+    out of reach in Python and the relabelling identity of
+    color_matrix_relabelled is used (an int64 array; the identity is checked
+    against the entry-by-entry evaluation for small n in the tests).
     """
+    if n > 6:
+        return color_matrix_relabelled(n)
     perms = gluon_orderings(n)
     m = len(perms)
     C = [[None] * m for _ in range(m)]

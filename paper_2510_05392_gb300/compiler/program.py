@@ -22,6 +22,8 @@ wavefunctions.
 """
 from __future__ import annotations
 
+import heapq
+
 from dataclasses import dataclass, field
 
 from .diagrams import Process, process
@@ -319,7 +321,10 @@ def build_program(n: int, order: str = "middle") -> Program:
         for o in ins:
             last_use[o] = i
     slot_of = {}
+    # free slots per pool: a min-heap (the lowest free slot is reused first)
+    # and the same slots as a set for membership tests
     free = {"G": [], "F": [], "B": [], "A": []}
+    free_set = {k: set() for k in free}
     nslot = {"G": 0, "F": 0, "B": 0, "A": 0}
     records = []
     for i, (code, outs, ins, extra) in enumerate(B.ops):
@@ -330,8 +335,8 @@ def build_program(n: int, order: str = "middle") -> Program:
             if o not in last_use and pl != "A":
                 raise AssertionError("unused wavefunction")
             if free[pl]:
-                free[pl].sort(reverse=True)
-                s_ = free[pl].pop()
+                s_ = heapq.heappop(free[pl])
+                free_set[pl].discard(s_)
             else:
                 s_ = nslot[pl]
                 nslot[pl] += 1
@@ -341,8 +346,9 @@ def build_program(n: int, order: str = "middle") -> Program:
         # an accumulator dies at its group's final (scattering) member
         for o in set(ins) | set(outs):
             if last_use.get(o, i) == i and (o in ins or (extra and len(extra) == 5 and extra[3] & 8)):
-                if o in slot_of and slot_of[o] not in free[pool_of[o]]:
-                    free[pool_of[o]].append(slot_of[o])
+                if o in slot_of and slot_of[o] not in free_set[pool_of[o]]:
+                    heapq.heappush(free[pool_of[o]], slot_of[o])
+                    free_set[pool_of[o]].add(slot_of[o])
         records.append(_record(code, out_slots, in_slots, extra))
     assert nslot["B"] <= 1
     prog = Program(n=n, npar=n + 2, ncolor=len(perms), ops=records, scatter=scatter,

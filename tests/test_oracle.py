@@ -93,6 +93,28 @@ def test_color_matrix_symmetric_psd(n):
 
 # ------------------------------------------------------------ diagrams -----
 
+@pytest.mark.parametrize("n", [3, 4, 5])
+def test_color_matrix_relabelling_equals_entrywise(n):
+    """The n! -trace construction used beyond 6 gluons reproduces the
+    entry-by-entry trace evaluation exactly."""
+    full, D, _ = color.color_matrix(n)
+    rel, D2, _ = color.color_matrix_relabelled(n)
+    assert D == D2
+    assert np.array_equal(np.array(full, dtype=np.int64), rel)
+
+
+def test_color_matrix_seven_gluons():
+    """2 -> 7 (5040 flows): symmetric, and every diagonal entry is the
+    textbook sum over colours of |(t^a1 ... t^a7)_ij|^2 = N C_F^7."""
+    from fractions import Fraction
+    Chat, D, perms = color.color_matrix(7)
+    assert Chat.shape == (5040, 5040) and len(perms) == 5040
+    assert np.array_equal(Chat, Chat.T)
+    diag = np.diag(Chat)
+    assert (diag == diag[0]).all()
+    assert Fraction(int(diag[0]), D) == 3 * Fraction(4, 3) ** 7
+
+
 def test_counts_against_paper_table():
     g = json.load(open(GOLDEN))["processes"]
     for proc, row in g.items():
@@ -183,6 +205,16 @@ def test_bose_symmetry_with_width(ng):
     for perm in list(itertools.permutations(range(4, 4 + ng)))[1:3]:
         q = p[:, [0, 1, 2, 3] + list(perm)]
         assert np.abs(oracle.me(q) / m - 1).max() < 1e-12
+
+
+def test_bose_symmetry_seven_gluons():
+    """g g -> t t~ + 5 g: exchanging the incoming gluons or two final gluons
+    leaves |M|^2 unchanged (one event, about 15 s of oracle time)."""
+    p = ps.generate(1, 5, 2000.0, 424242, ptmin=20.0, drmin=0.4)
+    m = oracle.me(p)
+    assert m[0] > 0
+    assert abs(oracle.me(p[:, [1, 0] + list(range(2, 9))])[0] / m[0] - 1) < 1e-12
+    assert abs(oracle.me(p[:, [0, 1, 2, 3, 8, 5, 6, 7, 4]])[0] / m[0] - 1) < 1e-12
 
 
 def test_helicity_sum_equals_total():

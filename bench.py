@@ -41,7 +41,11 @@ WORKLOADS = {
     "ggttgg_524288": ("g g > t t~ g g", 2, 524288, 1500.0, True, 20251005 + 2),
     "ggtt_16384": ("g g > t t~", 0, 16384, 1000.0, False, 20251005 + 1),
     "ggttggg_262144": ("g g > t t~ g g g", 3, 262144, 1500.0, True, 20251005 + 3),
+    # 2 -> 7 (5040 flows): state in HBM, FP64 colour sum kernel of its own
+    "ggttggggg_256": ("g g > t t~ g g g g g", 5, 256, 2000.0, True, 20251005 + 6),
 }
+# oracle events per CPU sample where one event takes seconds on the host
+CPU_SAMPLE_CAP = {"ggttggggg_256": 4}
 TEST_SEED = 12345  # helicity-filter test events
 
 
@@ -175,7 +179,7 @@ def cpu_baseline(name, nsample, steps=1):
     events of the workload; returns (events/s, threads, seconds)."""
     import oracle
     mom = _events(name, nsample)
-    oracle.me(mom[:8])  # load/compile, warm
+    oracle.me(mom[:1])  # load/compile, warm
     t0 = time.perf_counter()
     for _ in range(steps):
         oracle.me(mom)
@@ -188,10 +192,10 @@ def run_reference(args):
     if rank != 0:
         return
     name = args.workload
-    n = args.ref_sample
+    n = min(args.ref_sample, CPU_SAMPLE_CAP.get(name, args.ref_sample))
     import oracle
     mom = _events(name, n)
-    oracle.me(mom[:8])
+    oracle.me(mom[:min(8, n)])
     for _ in range(args.warmup):
         oracle.me(mom[: max(1, n // 8)])
     t0 = time.perf_counter()
@@ -474,16 +478,30 @@ def run_ours(args):
     # algorithmic FP64 work of the diagram kernel per step (mixed: the colour
     # sum runs on the tensor cores, so only the diagram work is FP64), over
     # the diagram kernel's own device time
-    fp64_colour = info.flops_colour if args.precision == "fp64" else 0.0
+    colour_ms, colour_n = kt["colour"]
+    separate_colour = colour_n > 0       # the colour sum runs in a kernel of its own
+    fp64_colour = info.flops_colour if (args.precision == "fp64" and not separate_colour) else 0.0
     flops_step = nevt * ngood * (info.flops_diagram + fp64_colour)
     diag_ms, diag_n = kt["diagram"]
     per_step = diag_n // args.steps
     achieved = flops_step * args.steps / (diag_ms / 1e3)
     roof_tc = None
+    roof_colour = None
+    if args.precision == "fp64" and separate_colour:
+        # FP64 colour-sum kernel (table-file processes): algorithmic FP64
+        # flops of the triangular quadratic form over its own device time
+        c_flops = nevt * ngood * info.flops_colour
+        c_ach = c_flops * args.steps / (colour_ms / 1e3)
+        roof_colour = {"bound": "alu", "achieved": c_ach / 1e12,
+                       "peak": fp64_peak / 1e12 if fp64_peak else None, "unit": "TFLOP/s",
+                       "frac": c_ach / fp64_peak if fp64_peak else None, "traffic": None,
+                       "kernel": "k_colour_big (FP64 pipe; peak = FP64 FMA probe, measured live)",
+                       "launches_per_step": colour_n // args.steps,
+                       "ms_per_step": colour_ms / args.steps, "flops_per_step": c_flops}
     if args.precision == "mixed":
         # tensor-core colour sum: bound by reading the BF16 jamp pieces once,
         # 2 (re, im) x 3 pieces x ncolor x 2 bytes per event and good helicity
-        tc_ms, tc_n = kt["colour_tc"]
+        tc_ms, tc_n = kt["colour"]
         bytes_step = nevt * ngood * 2 * 3 * info.ncolor * 2
         tc_ach = bytes_step * args.steps / (tc_ms / 1e3) / 1e9
         hbm = _measured_peak("hbm_gbs")
@@ -531,9 +549,10 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        v, cores, dt = cpu_baseline(name, args.cpu_sample)
+        ns = min(args.cpu_sample, CPU_SAMPLE_CAP.get(name, args.cpu_sample))
+        v, cores, dt = cpu_baseline(name, ns)
         cpu = {"value": v, "unit": "events/s", "cores": cores, "kind": "oracle",
-               "sample": f"first {args.cpu_sample} events of {name}, {dt:.1f} s"}
+               "sample": f"first {ns} events of {name}, {dt:.1f} s"}
 
     if rank == 0:
         line = {
@@ -553,11 +572,13 @@ def run_ours(args):
                          "frac": achieved / fp64_peak if fp64_peak else None,
                          "traffic": _traffic("k_sigmakin", name, nevt / per_step)
                          if per_step == 1 or args.precision == "fp64" else None,
-                         "kernel": "k_sigmakin (FP64 pipe; peak = FP64 FMA probe, measured live)",
+                         "kernel": ("k_sigmakin_big" if separate_colour and args.precision == "fp64"
+                                    else "k_sigmakin") + " (FP64 pipe; peak = FP64 FMA probe, measured live)",
                          "flops_per_launch": flops_step / per_step,
                          "launches_per_step": per_step,
                          "ms_per_step": diag_ms / args.steps},
             "roofline_colour_tc": roof_tc,
+            "roofline_colour_f64": roof_colour,
             "e2e": e2e,
             "gpu_launches": n_launches,
             "clocks": clk,

@@ -93,6 +93,22 @@ typedef struct {
  * alphas 0.118, filtered helicities, FP64). */
 int mg_process_create(const char *process, const mg_params *params, mg_process **out);
 
+/* Create g g > t t~ g g g g g (2 -> 7: 5040 colour flows; the paper could
+ * build it for CPUs only, Table "ggtt5g") from the binary table file the
+ * process compiler writes (compiler/emit.py emit_blob: "MGPROC01" header,
+ * program, jamp scatter, colour row by relative ordering, flow orderings).
+ * Every index of the program is checked against its pools before anything
+ * reaches the device; a damaged or foreign file gives MG_ERR_BAD_PROCESS.
+ * Runs with its wavefunction state in HBM (about 1.9 MB per thread, two
+ * 128-thread blocks per SM while half the free memory holds them) and an
+ * FP64 colour sum over the block upper triangle of the 5040 x 5040 colour
+ * matrix (built on the device, 203 MB).  FP64 only (MG_MIXED_BF16:
+ * MG_ERR_UNSUPPORTED); mg_sigmakin, mg_sigmakin_hel, mg_filter_helicities,
+ * mg_color_matrix and the timing hooks work as for the other processes;
+ * mg_sigmakin_ex, the batch calls and mg_filter_helicities_noalloc return
+ * MG_ERR_UNSUPPORTED. */
+int mg_process_create_from_tables(const char *table_path, const mg_params *params, mg_process **out);
+
 /* Helicity filter (Sec. 2.2 and Sec. 4.6 of the paper: keep the helicities with
  * a non-zero contribution).  Evaluates all 2^npar helicities in parallel on
  * the n test events momenta_dev[n][npar][4] and keeps h when

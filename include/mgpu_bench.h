@@ -29,8 +29,8 @@ int mg_debug_inject_stall(struct mg_process *p, unsigned int extra_bytes);
  * call on p then records a pair on the caller's stream around each of its
  * kernel launches.  n = 0 switches timing off and destroys the
  * events.  mg_kernel_times waits for the last recorded event and writes per
- * kind (0 diagram kernel k_sigmakin, 1 tensor-core colour sum, 2 per-event
- * sum of the mixed path) the summed device milliseconds ms_out[3] and the
+ * kind (0 diagram kernel, 1 colour-sum kernel: the tensor-core one of the
+ * mixed path or the FP64 one of a table-file process, 2 per-event sum) the summed device milliseconds ms_out[3] and the
  * launch counts launches_out[3] since the last reset; reset != 0 starts
  * over.  More than n launches between resets: MG_ERR_UNSUPPORTED (nothing
  * is reported).  Not thread-safe per process, like the other calls. */

@@ -61,6 +61,7 @@ _lib = None
 _VP = ctypes.c_void_p
 _SIGS = {
     "mg_process_create": ([ctypes.c_char_p, ctypes.POINTER(mg_params), ctypes.POINTER(_VP)], ctypes.c_int),
+    "mg_process_create_from_tables": ([ctypes.c_char_p, ctypes.POINTER(mg_params), ctypes.POINTER(_VP)], ctypes.c_int),
     "mg_filter_helicities": ([_VP, _VP, ctypes.c_int64, _VP, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "mg_sigmakin": ([_VP, _VP, ctypes.c_int64, _VP, _VP], ctypes.c_int),
     "mg_sigmakin_hel": ([_VP, _VP, ctypes.c_int64, _VP, _VP, _VP], ctypes.c_int),
@@ -119,6 +120,9 @@ def _stream(stream):
     return ctypes.c_void_p(getattr(stream, "cuda_stream", stream))
 
 
+TABLE_FILE_PROCESS = "g g > t t~ g g g g g"
+
+
 class Process:
     """Owner of one mg_process handle."""
 
@@ -126,8 +130,17 @@ class Process:
                  hel_mode=MG_HEL_FILTERED, precision=MG_FP64):
         self._h = _VP()
         self.params = mg_params(mt, wt, alphas, hel_mode, precision)
-        _check(lib().mg_process_create(process.encode(), ctypes.byref(self.params),
-                                       ctypes.byref(self._h)), "mg_process_create")
+        if " ".join(process.split()) == TABLE_FILE_PROCESS:
+            # too large to compile into the library: tables from the process
+            # compiler's binary file (generated once, a few minutes)
+            from . import build
+            path = build.process_tables(7)
+            _check(lib().mg_process_create_from_tables(path.encode(), ctypes.byref(self.params),
+                                                       ctypes.byref(self._h)),
+                   "mg_process_create_from_tables")
+        else:
+            _check(lib().mg_process_create(process.encode(), ctypes.byref(self.params),
+                                           ctypes.byref(self._h)), "mg_process_create")
         self.process = process
 
     @property
@@ -176,11 +189,12 @@ class Process:
 
     def kernel_times(self, reset=True):
         """{kind: (device ms summed, launches)} since the last reset for the
-        kinds 'diagram', 'colour_tc', 'event_sum' (waits for the events)."""
+        kinds 'diagram', 'colour' (the colour-sum kernel of the mixed path
+        or of a table-file process), 'event_sum' (waits for the events)."""
         ms = (ctypes.c_double * 3)()
         n = (ctypes.c_int * 3)()
         _check(lib().mg_kernel_times(self._h, int(reset), ms, n), "mg_kernel_times")
-        return {k: (ms[i], n[i]) for i, k in enumerate(("diagram", "colour_tc", "event_sum"))}
+        return {k: (ms[i], n[i]) for i, k in enumerate(("diagram", "colour", "event_sum"))}
 
     def sigmakin_ex(self, momenta, out=None, alphas=None, channel=-1, sde=None, flow=None,
                     rnd_hel=None, hel_out=None, rnd_col=None, col_out=None, stream=None):

@@ -38,6 +38,20 @@ def generate_tables(force: bool = False) -> None:
     os.replace(inc + ".tmp", inc)
 
 
+def process_tables(ngluon: int, force: bool = False) -> str:
+    """Binary table file of a process too large to compile into the library
+    (g g > t t~ + 5 g), written by the process compiler on first use (about
+    three minutes) and kept in _build/tables until the compiler changes."""
+    tdir = os.path.join(BUILD, "tables")
+    os.makedirs(tdir, exist_ok=True)
+    path = os.path.join(tdir, f"proc_{ngluon}g.bin")
+    srcs = glob.glob(os.path.join(HERE, "compiler", "*.py"))
+    if force or not os.path.exists(path) or os.path.getmtime(path) < _newest(srcs):
+        from .compiler import emit
+        emit.emit_blob(ngluon, path)
+    return path
+
+
 def _compile(src: str, obj: str, deps) -> str:
     if os.path.exists(obj) and os.path.getmtime(obj) >= _newest([src] + deps):
         return obj

@@ -65,6 +65,18 @@ def chain_trace(word) -> Fraction:
     return total / 2 ** len(pairs)
 
 
+def relative_row(n: int):
+    """(row, D): row[k] = D * C_(id, r) for the k-th ordering r in
+    itertools.permutations order, so that C_st = row[rank(r)] with
+    r_k = (position in s of t_k).  n! traces."""
+    perms = list(itertools.permutations(range(n)))
+    base = [chain_trace(tuple(reversed(range(n))) + tuple(r)) for r in perms]
+    D = 1
+    for x in base:
+        D = D * x.denominator // math.gcd(D, x.denominator)
+    return [int(x * D) for x in base], D
+
+
 def colour_matrix(n: int):
     """(C_hat rows as ints, D, orderings) for n gluons, orderings in
     itertools.permutations order of range(n)."""

@@ -7,11 +7,17 @@ For every supported process the generated include file holds:
 and one registry row with the sizes, the common denominator D, the averaging
 factor and the algorithmic FP64 operation counts per helicity.
 
+Processes too large to compile in (g g > t t~ + 5 g: 810k ops, 5040 flows)
+are written instead as a binary table file that the library loads at run
+time (emit_blob; format below).
+
 Usage: python -m paper_2510_05392_gb300.compiler.emit OUT.inc [maxgluons]
+       python -m paper_2510_05392_gb300.compiler.emit --blob OUT.bin ngluons
 """
 from __future__ import annotations
 
 import math
+import struct
 import sys
 
 from . import colour, program
@@ -129,5 +135,38 @@ def emit(path: str, max_gluons: int = 6, list_path: str | None = None) -> None:
                 "#pragma once\n#define MG_PROC_LIST(X) " + " ".join(xlist) + "\n")
 
 
+# Binary process table (little-endian), read by mg_process_create_from_tables:
+#   char[8]  "MGPROC01"
+#   int32[12] version (1), ngluon, npar, ncolor, nops, nscat, nslot (gluon),
+#             nslot_top, nslot_acc, ncolour_groups, ndiagrams, nterms
+#   int64    D (common denominator);  float64 iden, flops_diagram, flops_colour
+#   int32    ops[nops][8];  int32 scat[nscat]
+#   int64    row[ncolor]    D * C_(id, r) by relative ordering r (colour.relative_row)
+#   int8     perms[ncolor][ngluon]   the flow orderings, itertools order
+BLOB_MAGIC = b"MGPROC01"
+
+
+def emit_blob(n: int, path: str) -> None:
+    prog = program.build_program(n)
+    row, D = colour.relative_row(n)
+    fl = algorithmic_flops(prog)
+    iden = 256 * math.factorial(n - 2)
+    with open(path + ".tmp", "wb") as f:
+        f.write(BLOB_MAGIC)
+        f.write(struct.pack("<12i", 1, n, n + 2, prog.ncolor, len(prog.ops), len(prog.scatter),
+                            prog.nslot, prog.nslot_f, max(1, prog.nslot_acc), prog.ncolour_groups,
+                            prog.ndiagrams, prog.nterms))
+        f.write(struct.pack("<q3d", D, float(iden), float(fl["diagram"]), float(fl["colour"])))
+        f.write(struct.pack(f"<{8 * len(prog.ops)}i", *[v for r in prog.ops for v in r]))
+        f.write(struct.pack(f"<{len(prog.scatter)}i", *prog.scatter))
+        f.write(struct.pack(f"<{len(row)}q", *row))
+        f.write(bytes(v for p in prog.perms for v in p))
+    import os
+    os.replace(path + ".tmp", path)
+
+
 if __name__ == "__main__":
-    emit(sys.argv[1], int(sys.argv[2]) if len(sys.argv) > 2 else 6)
+    if sys.argv[1] == "--blob":
+        emit_blob(int(sys.argv[3]), sys.argv[2])
+    else:
+        emit(sys.argv[1], int(sys.argv[2]) if len(sys.argv) > 2 else 6)

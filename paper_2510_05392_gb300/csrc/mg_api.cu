@@ -93,6 +93,19 @@ void free_proc(mg_process *p) {
     for (int i = 0; i < 2 * p->tcap; i++) cudaEventDestroy(p->tev[i]);
     free(p->tev);
     free(p->tkind);
+    cudaFree(p->d_crow);
+    cudaFree(p->d_cperm);
+    cudaFree(p->d_cbig);
+    cudaFree(p->d_scratch);
+    cudaFree(p->d_jrow);
+    cudaFree(p->d_qpart);
+    if (p->own_tab) {
+        free((void *)p->own_tab->ops);
+        free((void *)p->own_tab->scat);
+        free((void *)p->own_tab->crow);
+        free((void *)p->own_tab->cperm);
+        free(p->own_tab);
+    }
     free(p);
 }
 
@@ -101,7 +114,7 @@ void free_proc(mg_process *p) {
 // combinations (bit 2*bt + btb).
 int set_hel_list(mg_process *p, const uint8_t *mask) {
     const int npar = p->tab->npar, ng = p->tab->ngluon;
-    int units[64];
+    int units[128];
     int nu = 0, ngood = 0;
     for (int h = 0; h < (1 << npar); h++) p->mask[h] = mask[h] ? 1 : 0;
     for (int g = 0; g < (1 << ng); g++) {
@@ -154,6 +167,199 @@ int setup_mixed(mg_process *p) {
     free(h);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? MG_ERR_NO_MEMORY : cuda_fail(e);
     return MG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Processes loaded from a table file and run with their state in HBM
+// (mg_big.cu): chunks of events whose FP64 jamp rows fit 12 GiB; per chunk
+// the rows are cleared, the diagram kernel accumulates the jamps into them,
+// the colour-sum kernel forms every row's quadratic form per 64-colour tile
+// and the event sum adds them up.
+int sigmakin_big(mg_process *p, const double *mom, int64_t nevt, double *me, double *me_hel,
+                 cudaStream_t s) {
+    const mg_proc_table *t = p->tab;
+    const int nu = p->nunits;
+    const int nhel = 1 << t->npar;
+    if (nevt <= 0) return MG_OK;
+    if (nu == 0) {
+        if (me) MG_CUDA(cudaMemsetAsync(me, 0, sizeof(double) * nevt, s));
+        return MG_OK;
+    }
+    const long long np = p->big_np;
+    const int ntile = (int)(np / 64);
+    const long long row_limit = (12LL << 30) / (np * 8);      // rows of 12 GiB
+    long long ev_chunk = row_limit / (8LL * nu);
+    if (ev_chunk < 1) ev_chunk = 1;
+    if (ev_chunk > nevt) ev_chunk = nevt;
+    const long long nipad_max = (ev_chunk * nu + 7) / 8 * 8;
+    // threads: two 128-thread CTAs per SM while the device has room for their
+    // state, never more than the items of a chunk
+    int nsm = 0;
+    MG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device));
+    const int blk = mg_big_block();
+    const size_t state = mg_big_state_bytes(t->nslot, t->nslot_top, t->nslot_acc);
+    long long T = p->big_threads;
+    if (T <= 0) {
+        size_t freeb = 0, totalb = 0;
+        MG_CUDA(cudaMemGetInfo(&freeb, &totalb));
+        const long long have = p->scratch_threads;
+        T = 2LL * nsm * blk;
+        while (T > blk && T > have && (size_t)(T - have) * state > freeb / 2) T -= blk;
+    }
+    const long long need = (nipad_max + blk - 1) / blk * blk;
+    if (T > need) T = need;
+    if (T > p->scratch_threads) {
+        cudaFree(p->d_scratch);
+        p->d_scratch = nullptr;
+        p->scratch_threads = 0;
+        cudaError_t e = cudaMalloc(&p->d_scratch, (size_t)T * state);
+        if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? MG_ERR_NO_MEMORY : cuda_fail(e);
+        p->scratch_threads = T;
+    }
+    if (nipad_max > p->jrow_items) {
+        cudaFree(p->d_jrow);
+        cudaFree(p->d_qpart);
+        p->d_jrow = nullptr;
+        p->d_qpart = nullptr;
+        p->jrow_items = 0;
+        cudaError_t e = cudaMalloc(&p->d_jrow, sizeof(double) * np * 8 * nipad_max);
+        if (e == cudaSuccess) e = cudaMalloc(&p->d_qpart, sizeof(double) * ntile * 8 * nipad_max);
+        if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? MG_ERR_NO_MEMORY : cuda_fail(e);
+        p->jrow_items = nipad_max;
+    }
+    const mg_dev_proc dp = dev_view(p);
+    for (long long e0 = 0; e0 < nevt; e0 += ev_chunk) {
+        const long long n = (nevt - e0 < ev_chunk) ? nevt - e0 : ev_chunk;
+        const long long nitem = n * nu;
+        const long long nip = (nitem + 7) / 8 * 8;
+        const long long R = 8 * nip;
+        MG_CUDA(cudaMemsetAsync(p->d_jrow, 0, sizeof(double) * np * R, s));
+        int slot = mg_timer_begin(p, s, MG_KT_DIAGRAM);
+        MG_CUDA(mg_launch_sigmakin_big(dp, mom + e0 * t->npar * 4, nitem, p->d_units, nu, t->nslot,
+                                       t->nslot_top, p->d_scratch, T, p->d_jrow, R, nip, s));
+        mg_timer_end(p, s, slot);
+        slot = mg_timer_begin(p, s, MG_KT_COLOUR);
+        MG_CUDA(mg_launch_colour_big(p->d_jrow, R, p->d_cbig, (int)np, p->d_qpart, s));
+        mg_timer_end(p, s, slot);
+        slot = mg_timer_begin(p, s, MG_KT_EVENT_SUM);
+        MG_CUDA(mg_launch_event_sum_big(p->d_qpart, R, ntile, nip, p->d_units, nu, n, p->factor,
+                                        me ? me + e0 : nullptr, me_hel ? me_hel + e0 * nhel : nullptr,
+                                        s));
+        mg_timer_end(p, s, slot);
+    }
+    return MG_OK;
+}
+
+// Checks every index a table-file program can use against its pools, so a
+// damaged file is rejected on the host instead of addressing out of bounds.
+bool valid_program(const mg_proc_table *t) {
+    const int ng = t->ngluon, nsub = 1 << ng;
+    const int nsg = t->nslot, nsf = t->nslot_top, nsa = t->nslot_acc;
+    auto in = [](int x, int n) { return x >= 0 && x < n; };
+    for (int i = 0; i < t->nops; i++) {
+        const int32_t *r = t->ops + 8 * i;
+        const int c = r[0], ay = r[1], az = r[2], aw = r[3], bx = r[4], by = r[5], bz = r[6], bw = r[7];
+        bool ok;
+        switch (c) {
+            case MG_OP_EXT_G: ok = in(ay, nsg) && in(az, t->npar) && az != 2 && az != 3; break;
+            case MG_OP_EXT_UB:
+            case MG_OP_EXT_V: ok = in(ay, nsf); break;
+            case MG_OP_V3: ok = in(ay, nsg) && in(az, nsg) && in(aw, nsg) && in(bx, nsub) && in(by, nsub); break;
+            case MG_OP_V4:
+                ok = in(ay, nsg) && in(az, nsg) && in(aw, nsg) && in(bx, nsg) && in(by, nsg) &&
+                     in(bz, nsg) && in(bw, nsub);
+                break;
+            case MG_OP_FPRE:
+            case MG_OP_FSUF: ok = in(ay, nsf) && in(az, nsf) && in(aw, nsg) && in(bx, nsub); break;
+            case MG_OP_XROW: ok = in(ay, nsf) && in(az, nsf) && in(aw, nsg); break;
+            case MG_OP_YCOL: ok = in(ay, nsf) && in(az, nsg) && in(aw, nsf); break;
+            case MG_OP_BIL: ok = in(az, nsf) && in(aw, nsf); break;
+            case MG_OP_AMP_SS:
+            case MG_OP_AMP_VV:
+                ok = (c == MG_OP_AMP_SS ? in(az, nsf) && in(aw, nsf) : in(aw, nsg)) && bx >= 0 &&
+                     by >= 0 && (long long)bx + by <= t->nscat && (bz == -1 || in(bz, nsa));
+                break;
+            default: ok = false;
+        }
+        if (!ok) return false;
+    }
+    for (int i = 0; i < t->nscat; i++)
+        if (t->scat[i] < 0 || (t->scat[i] >> 2) >= t->ncolor) return false;
+    for (int a = 0; a < t->ncolor; a++) {
+        unsigned seen = 0;
+        for (int q = 0; q < ng; q++) {
+            const int x = t->cperm[a * ng + q];
+            if (x < 0 || x >= ng || ((seen >> x) & 1u)) return false;
+            seen |= 1u << x;
+        }
+    }
+    return true;
+}
+
+mg_proc_table *read_table_file(const char *path, int *status) {
+    *status = MG_ERR_BAD_PROCESS;
+    FILE *f = fopen(path, "rb");
+    if (!f) return nullptr;
+    char magic[8];
+    int32_t h[12];
+    int64_t den;
+    double dv[3];
+    mg_proc_table *t = (mg_proc_table *)calloc(1, sizeof(mg_proc_table));
+    bool ok = t && fread(magic, 1, 8, f) == 8 && memcmp(magic, "MGPROC01", 8) == 0 &&
+              fread(h, sizeof(int32_t), 12, f) == 12 && fread(&den, 8, 1, f) == 1 &&
+              fread(dv, 8, 3, f) == 3;
+    if (ok) {
+        ok = h[0] == 1 && h[1] == mg_big_ngluon() && h[2] == h[1] + 2 && h[3] > 0 && h[4] > 0 &&
+             h[5] >= 0 && h[6] > 0 && h[7] > 0 && h[8] > 0 && den > 0;
+        long long fact = 1;
+        for (int i = 2; i <= h[1]; i++) fact *= i;
+        ok = ok && h[3] == fact;
+    }
+    if (ok) {
+        t->ngluon = h[1];
+        t->npar = h[2];
+        t->ncolor = h[3];
+        t->nops = h[4];
+        t->nscat = h[5];
+        t->nslot = h[6];
+        t->nslot_top = h[7];
+        t->nslot_acc = h[8];
+        t->ndiagrams = h[10];
+        t->nterms = h[11];
+        t->denom = den;
+        t->iden = dv[0];
+        t->flops_diagram = dv[1];
+        t->flops_colour = dv[2];
+        int32_t *ops = (int32_t *)malloc(sizeof(int32_t) * 8 * (size_t)t->nops);
+        int32_t *scat = (int32_t *)malloc(sizeof(int32_t) * (t->nscat > 0 ? t->nscat : 1));
+        int64_t *row = (int64_t *)malloc(sizeof(int64_t) * t->ncolor);
+        int8_t *perm = (int8_t *)malloc((size_t)t->ncolor * t->ngluon);
+        t->ops = ops;
+        t->scat = scat;
+        t->crow = row;
+        t->cperm = perm;
+        ok = ops && scat && row && perm &&
+             fread(ops, sizeof(int32_t), 8 * (size_t)t->nops, f) == 8 * (size_t)t->nops &&
+             fread(scat, sizeof(int32_t), t->nscat, f) == (size_t)t->nscat &&
+             fread(row, sizeof(int64_t), t->ncolor, f) == (size_t)t->ncolor &&
+             fread(perm, 1, (size_t)t->ncolor * t->ngluon, f) == (size_t)t->ncolor * t->ngluon &&
+             fgetc(f) == EOF && valid_program(t);
+    }
+    fclose(f);
+    if (!ok) {
+        if (t) {
+            free((void *)t->ops);
+            free((void *)t->scat);
+            free((void *)t->crow);
+            free((void *)t->cperm);
+            free(t);
+        }
+        return nullptr;
+    }
+    t->name = "ggttggggg";
+    t->process = "g g > t t~ g g g g g";
+    *status = MG_OK;
+    return t;
 }
 
 int pow2_at_least(int x) {
@@ -252,7 +458,7 @@ int mg_process_create(const char *process, const mg_params *params, mg_process *
     TRY(cudaMalloc(&p->d_ops, sizeof(int32_t) * 8 * t->nops));
     TRY(cudaMalloc(&p->d_scat, sizeof(int32_t) * (t->nscat > 0 ? t->nscat : 1)));
     TRY(cudaMalloc(&p->d_cup, sizeof(double) * ntri));
-    TRY(cudaMalloc(&p->d_units, sizeof(int) * 64));
+    TRY(cudaMalloc(&p->d_units, sizeof(int) * 128));
     TRY(cudaMemcpy(p->d_ops, t->ops, sizeof(int32_t) * 8 * t->nops, cudaMemcpyHostToDevice));
     if (t->nscat > 0)
         TRY(cudaMemcpy(p->d_scat, t->scat, sizeof(int32_t) * t->nscat, cudaMemcpyHostToDevice));
@@ -266,7 +472,7 @@ int mg_process_create(const char *process, const mg_params *params, mg_process *
 #undef TRY
     free(cup);
     if (par.hel_mode == MG_HEL_ALL) {
-        uint8_t all[256];
+        uint8_t all[512];
         memset(all, 1, sizeof(all));
         st = set_hel_list(p, all);
         if (st != MG_OK) {
@@ -280,6 +486,71 @@ fail:
     free(cup);
     free_proc(p);
     return st;
+}
+
+int mg_process_create_from_tables(const char *path, const mg_params *params, mg_process **out) {
+    if (!path || !out) return MG_ERR_BAD_ARG;
+    *out = nullptr;
+    mg_params par = {173.0, 1.4915, 0.118, MG_HEL_FILTERED, MG_FP64};
+    if (params) par = *params;
+    if (!(par.mt > 0.0) || !(par.wt >= 0.0) || !(par.alphas > 0.0)) return MG_ERR_BAD_ARG;
+    if (par.hel_mode != MG_HEL_FILTERED && par.hel_mode != MG_HEL_ALL) return MG_ERR_BAD_ARG;
+    if (par.precision != MG_FP64) return MG_ERR_UNSUPPORTED;
+    int st = MG_OK;
+    mg_proc_table *t = read_table_file(path, &st);
+    if (!t) return st;
+    mg_process *p = (mg_process *)calloc(1, sizeof(mg_process));
+    if (!p) {
+        free((void *)t->ops);
+        free((void *)t->scat);
+        free((void *)t->crow);
+        free((void *)t->cperm);
+        free(t);
+        return MG_ERR_NO_MEMORY;
+    }
+    p->own_tab = t;
+    p->tab = t;
+    p->big = 1;
+    p->table_index = -1;
+    p->par = par;
+    p->ngood = -1;
+    p->tpe = 1;
+    p->block = mg_big_block();
+    const double gs = sqrt(4.0 * M_PI * par.alphas);
+    p->factor = pow(gs, 2 * t->ngluon) / (t->iden * (double)t->denom);
+    p->big_np = 64 * ((t->ncolor + 63) / 64);
+    const size_t np = (size_t)p->big_np;
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_ops, sizeof(int32_t) * 8 * t->nops);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_scat, sizeof(int32_t) * (t->nscat > 0 ? t->nscat : 1));
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_units, sizeof(int) * 128);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_crow, sizeof(long long) * t->ncolor);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_cperm, (size_t)t->ncolor * t->ngluon);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_cbig, sizeof(double) * np * np);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_ops, t->ops, sizeof(int32_t) * 8 * t->nops, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && t->nscat > 0)
+        e = cudaMemcpy(p->d_scat, t->scat, sizeof(int32_t) * t->nscat, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_crow, t->crow, sizeof(long long) * t->ncolor, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_cperm, t->cperm, (size_t)t->ncolor * t->ngluon, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = mg_launch_build_cbig(p->d_crow, p->d_cperm, t->ncolor, (int)np, p->d_cbig, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        free_proc(p);
+        return e == cudaErrorMemoryAllocation ? MG_ERR_NO_MEMORY : cuda_fail(e);
+    }
+    if (par.hel_mode == MG_HEL_ALL) {
+        uint8_t all[512];
+        memset(all, 1, sizeof(all));
+        st = set_hel_list(p, all);
+        if (st != MG_OK) {
+            free_proc(p);
+            return st;
+        }
+    }
+    *out = p;
+    return MG_OK;
 }
 
 void mg_process_destroy(mg_process *p) { free_proc(p); }
@@ -308,6 +579,27 @@ int mg_process_info(const mg_process *p, mg_info *o) {
 int mg_color_matrix(const mg_process *p, int64_t *ints_out, int64_t *denom_out) {
     if (!p || !ints_out) return MG_ERR_BAD_ARG;
     const int nc = p->tab->ncolor;
+    if (!p->tab->chat) {   // table-file process: C_st = row[rank of s^-1 t]
+        const int ng = p->tab->ngluon;
+        for (int a = 0; a < nc; a++) {
+            int pos[16];
+            for (int q = 0; q < ng; q++) pos[p->tab->cperm[a * ng + q]] = q;
+            for (int b = 0; b < nc; b++) {
+                long long rank = 0;
+                unsigned used = 0;
+                for (int q = 0; q < ng; q++) {
+                    const int r = pos[p->tab->cperm[b * ng + q]];
+                    int smaller = 0;
+                    for (int x = 0; x < r; x++) smaller += !((used >> x) & 1u);
+                    rank = rank * (ng - q) + smaller;
+                    used |= 1u << r;
+                }
+                ints_out[(size_t)a * nc + b] = p->tab->crow[rank];
+            }
+        }
+        if (denom_out) *denom_out = p->tab->denom;
+        return MG_OK;
+    }
     for (int i = 0; i < nc * nc; i++) ints_out[i] = p->tab->chat[i];
     if (denom_out) *denom_out = p->tab->denom;
     return MG_OK;
@@ -341,13 +633,13 @@ int mg_filter_helicities(mg_process *p, const double *mom, int64_t n, void *stre
     cudaStream_t s = (cudaStream_t)stream;
     const int nhel = 1 << p->tab->npar;
     // evaluate every helicity: temporary list 0..nhel-1
-    uint8_t all[256];
+    uint8_t all[512];
     memset(all, 1, sizeof(all));
     st = set_hel_list(p, all);
     if (st) return st;
     double *mh = nullptr;
     unsigned char *dmask = nullptr;
-    uint8_t mask[256];
+    uint8_t mask[512];
     cudaError_t e = cudaMalloc(&mh, sizeof(double) * n * nhel);
     if (e != cudaSuccess) {
         p->ngood = -1;
@@ -355,8 +647,20 @@ int mg_filter_helicities(mg_process *p, const double *mom, int64_t n, void *stre
     }
     e = cudaMalloc(&dmask, nhel);
     if (e == cudaSuccess) e = cudaMemsetAsync(mh, 0, sizeof(double) * n * nhel, s);
-    if (e == cudaSuccess)
-        e = mg_launch_sigmakin(dev_view(p), mom, n, p->d_units, p->nunits, 32, p->block, nullptr, mh, s);
+    if (e == cudaSuccess) {
+        if (p->big) {
+            const int sb = sigmakin_big(p, mom, n, nullptr, mh, s);
+            if (sb != MG_OK) {
+                cudaFree(mh);
+                cudaFree(dmask);
+                p->ngood = -1;
+                return sb;
+            }
+        } else {
+            e = mg_launch_sigmakin(dev_view(p), mom, n, p->d_units, p->nunits, 32, p->block, nullptr,
+                                   mh, s);
+        }
+    }
     if (e == cudaSuccess) e = mg_launch_helmask(mh, n, nhel, 1e-14, dmask, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(mask, dmask, nhel, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -427,7 +731,7 @@ static int sigmakin_mixed(mg_process *p, const double *mom, int64_t nevt, double
         MG_CUDA(mg_launch_sigmakin(dp, mom + e0 * p->tab->npar * 4, n, p->d_units, p->nunits, tpe,
                                    p->block, nullptr, nullptr, s, p->d_jbuf, p->kp, nup));
         mg_timer_end(p, s, slot);
-        slot = mg_timer_begin(p, s, MG_KT_COLOUR_TC);
+        slot = mg_timer_begin(p, s, MG_KT_COLOUR);
         MG_CUDA(mg_launch_colorsum_tc(p->d_jbuf, used, p->kp, p->d_cmat, p->np, p->tab->ncolor,
                                       cpe, p->debug_extra_tx, p->d_part, p->d_err, s));
         mg_timer_end(p, s, slot);
@@ -458,6 +762,7 @@ static int sigmakin_impl(mg_process *p, const double *mom, int64_t nevt, double 
     }
     int tpe = p->tpe;
     while (tpe > 1 && tpe > p->nunits) tpe >>= 1;
+    if (p->big) return sigmakin_big(p, mom, nevt, me, me_hel, s);
     if (p->par.precision == MG_MIXED_BF16) {
         if (me_hel) return MG_ERR_UNSUPPORTED;
         return sigmakin_mixed(p, mom, nevt, me, tpe, s);
@@ -593,6 +898,7 @@ extern "C" int mg_filter_helicities_noalloc(mg_process *p, const double *mom, in
                                             void *stream, int *ngood_out) {
     if (!p) return MG_ERR_BAD_ARG;
     if (n < 1 || n > MG_NOALLOC_FILTER_MAX_EVENTS) return MG_ERR_BAD_ARG;
+    if (p->big) return MG_ERR_UNSUPPORTED;   // 512 helicities exceed the fixed scratch
     int cur = -1;
     if (cudaGetDevice(&cur) != cudaSuccess) return MG_ERR_CUDA;
     if (cur != p->device) return MG_ERR_BAD_ARG;
@@ -605,11 +911,11 @@ extern "C" int mg_filter_helicities_noalloc(mg_process *p, const double *mom, in
     const int nhel = 1 << p->tab->npar;
     double *mh = (double *)scratch;
     unsigned char *dmask = (unsigned char *)scratch + MG_NOALLOC_FILTER_MAX_EVENTS * 256 * sizeof(double);
-    uint8_t all[256];
+    uint8_t all[512];
     memset(all, 1, sizeof(all));
     st = set_hel_list(p, all);
     if (st) return st;
-    uint8_t mask[256];
+    uint8_t mask[512];
     // the array keeps the previous call's contents: clear what is read
     cudaError_t e = cudaMemsetAsync(mh, 0, sizeof(double) * n * nhel, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(dmask, 0, nhel, s);
@@ -659,7 +965,7 @@ extern "C" int mg_sigmakin_ex(mg_process *p, const double *mom, int64_t nevt,
                               const mg_sigmakin_extras *x, double *me, void *stream) {
     if (!p || !x || nevt < 0) return MG_ERR_BAD_ARG;
     if (p->ngood < 0) return MG_ERR_NOT_FILTERED;
-    if (p->par.precision != MG_FP64) return MG_ERR_UNSUPPORTED;
+    if (p->par.precision != MG_FP64 || p->big) return MG_ERR_UNSUPPORTED;
     if (nevt == 0) return MG_OK;
     int st = check_dev_ptr(mom, p->device);
     if (!st && me) st = check_dev_ptr(me, p->device);

@@ -1,0 +1,390 @@
+// Processes whose per-thread state does not fit in local memory: g g -> t t~
+// + 5 g (810k ops, 12527 gluon + 3989 top-line slots, 8505 accumulators and
+// 5040 colour flows: about 2 MB per work unit, above the 512 KB a thread
+// may hold in local memory).  The paper's CUDA build of this process failed
+// to link (its generated code is too large); here the same table-driven
+// program runs with its state in HBM, which the arithmetic still dominates:
+// about 150 FP64 flops per 200 bytes of state moved, right of the FP64 ridge
+// of a GB300.
+//
+// Three kernels per chunk of events:
+//   k_sigmakin_big  one thread per work item (event, gluon-helicity
+//                   configuration with its four top helicities), persistent
+//                   over the items.  Wavefunction slots and accumulators live
+//                   in a slot-major, thread-interleaved scratch (element i of
+//                   thread t at scratch[i * T + t], so a warp's accesses are
+//                   coalesced); the jamps accumulate directly into the FP64
+//                   colour-major rows of the colour sum, row
+//                   r = (2 v + re/im) * nipad + item, colour c at c * R + r.
+//   k_colour_big    the colour sum J^H C J (Sec. 3.3, Eq. "jcj") of every
+//                   row as a tiled FP64 quadratic form over the block upper
+//                   triangle of D*C (off-diagonal 64 x 64 blocks doubled, the
+//                   paper's triangular colour sum at tile granularity):
+//                   qpart[I][r] = sum_{n in tile I} V_rn sum_{k >= 64 I} Cb_nk V_rk.
+//   k_event_sum_big per event, the sum over its items, good helicity
+//                   combinations, real/imaginary rows and tiles in a fixed
+//                   order (and |M_h|^2 per helicity for the filter).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mg_dirac.cuh"
+#include "mg_internal.h"
+#include "mg_kin.cuh"
+
+using namespace mg;
+
+namespace {
+
+constexpr int BIG_NG = 7;
+constexpr int BIG_BLOCK = 128;
+constexpr int CT = 64;   // colour tile (n and k) of the quadratic form
+constexpr int CK = 16;   // k chunk per shared-memory stage
+constexpr int RT = 64;   // rows per tile
+
+// slot-major, thread-interleaved state; p already offset by the thread
+struct Strided {
+    double2 *p;
+    long long T;
+    __device__ __forceinline__ cx ld(long long i) const {
+        const double2 v = p[i * T];
+        return mk(v.x, v.y);
+    }
+    __device__ __forceinline__ void st(long long i, cx c) const { p[i * T] = make_double2(c.r, c.i); }
+    __device__ __forceinline__ void ld4(long long i0, cx *o) const {
+#pragma unroll
+        for (int m = 0; m < 4; m++) o[m] = ld(i0 + m);
+    }
+    __device__ __forceinline__ void st4(long long i0, const cx *o) const {
+#pragma unroll
+        for (int m = 0; m < 4; m++) st(i0 + m, o[m]);
+    }
+};
+
+// The program of one item (same ops and semantics as the local-memory
+// interpreter of mg_kernels.cu): pools G (slot s, component m: 4 s + m),
+// F (slot s, variant v, component m: 8 s + 4 v + m), A (slot s, variant v:
+// 4 s + v); jamp (c, v) real part at jr[c * R + 2 v * nipad], imaginary part
+// one row block further.
+template <int NG>
+__device__ void run_item(const Kin<NG> &k, int g, const int4 *__restrict__ ops, int nops,
+                         const int *__restrict__ scat, double mt, const Strided &WG,
+                         const Strided &WF, const Strided &ACC, double *__restrict__ jr, long long R,
+                         long long nipad) {
+    cx G0[4][4];
+    for (int i = 0; i < nops; i++) {
+        const int4 a = __ldg(ops + 2 * i);
+        const int4 b = __ldg(ops + 2 * i + 1);
+        switch (a.x) {
+            case MG_OP_EXT_G: {
+                const int gi = (a.z < 2) ? a.z : a.z - 2;
+                cx e[4];
+                ext_gluon(k.P[a.z], ((g >> gi) & 1) ? 1 : -1, a.w != 0, e);
+                WG.st4(4LL * a.y, e);
+                break;
+            }
+            case MG_OP_EXT_UB:
+            case MG_OP_EXT_V:
+                for (int v = 0; v < 2; v++) {
+                    cx o[4];
+                    if (a.x == MG_OP_EXT_UB)
+                        ext_ubar(k.P[2], v ? 1 : -1, o);
+                    else
+                        ext_v(k.P[3], v ? 1 : -1, o);
+                    WF.st4(8LL * a.y + 4 * v, o);
+                }
+                break;
+            case MG_OP_V3: {
+                cx j1[4], j2[4], o[4];
+                WG.ld4(4LL * a.z, j1);
+                WG.ld4(4LL * a.w, j2);
+                vvv_current(j1, k.K[b.x], j2, k.K[b.y], k.IP2[b.x | b.y], o);
+                WG.st4(4LL * a.y, o);
+                break;
+            }
+            case MG_OP_V4: {
+                cx x[4], y[4], z[4], o1[4], o2[4], o3[4];
+                WG.ld4(4LL * b.x, x);
+                WG.ld4(4LL * b.y, y);
+                WG.ld4(4LL * b.z, z);
+                vvvv_currents(x, y, z, k.IP2[b.w], o1, o2, o3);
+                WG.st4(4LL * a.y, o1);
+                WG.st4(4LL * a.z, o2);
+                WG.st4(4LL * a.w, o3);
+                break;
+            }
+            case MG_OP_FPRE:
+            case MG_OP_FSUF: {
+                cx jg[4];
+                WG.ld4(4LL * a.w, jg);
+                const Slash s = slash_blocks(jg);
+                const bool pre = a.x == MG_OP_FPRE;
+                const cx d = pre ? k.DP[b.x] : k.DS[b.x];
+                for (int v = 0; v < 2; v++) {
+                    cx in[4], t[4], o[4];
+                    WF.ld4(8LL * a.z + 4 * v, in);
+                    if (pre) {
+                        row_slash(in, s, t);
+                        row_qm(t, k.QP[b.x], mt, o);
+                    } else {
+                        slash_col(s, in, t);
+                        qm_col(k.QS[b.x], mt, t, o);
+                    }
+                    for (int m = 0; m < 4; m++) o[m] = o[m] * d;
+                    WF.st4(8LL * a.y + 4 * v, o);
+                }
+                break;
+            }
+            case MG_OP_XROW:
+            case MG_OP_YCOL: {
+                const bool xrow = a.x == MG_OP_XROW;
+                cx jg[4];
+                WG.ld4(4LL * (xrow ? a.w : a.z), jg);
+                const Slash s = slash_blocks(jg);
+                for (int v = 0; v < 2; v++) {
+                    cx in[4], o[4];
+                    WF.ld4(8LL * (xrow ? a.z : a.w) + 4 * v, in);
+                    if (xrow)
+                        row_slash(in, s, o);
+                    else
+                        slash_col(s, in, o);
+                    WF.st4(8LL * a.y + 4 * v, o);
+                }
+                break;
+            }
+            case MG_OP_BIL: {
+                cx u[2][4], w[2][4];
+                for (int v = 0; v < 2; v++) {
+                    WF.ld4(8LL * a.z + 4 * v, u[v]);
+                    WF.ld4(8LL * a.w + 4 * v, w[v]);
+                }
+                for (int bt = 0; bt < 2; bt++)
+                    for (int btb = 0; btb < 2; btb++) bilinear(u[bt], w[btb], G0[2 * bt + btb]);
+                break;
+            }
+            case MG_OP_AMP_SS:
+            case MG_OP_AMP_VV: {
+                cx amp[4];
+                if (a.x == MG_OP_AMP_SS) {
+                    cx x[2][4], y[2][4];
+                    for (int v = 0; v < 2; v++) {
+                        WF.ld4(8LL * a.z + 4 * v, x[v]);
+                        WF.ld4(8LL * a.w + 4 * v, y[v]);
+                    }
+                    for (int bt = 0; bt < 2; bt++)
+                        for (int btb = 0; btb < 2; btb++) amp[2 * bt + btb] = sdot(x[bt], y[btb]);
+                } else {
+                    cx w[4];
+                    WG.ld4(4LL * a.w, w);
+                    for (int v = 0; v < 4; v++) amp[v] = mdot(G0[v], w);
+                }
+                if (b.z >= 0) {  // member of a colour-factor group
+                    const int mode = b.w;
+                    for (int v = 0; v < 4; v++) {
+                        const cx t = unit_times(mode, amp[v]);
+                        amp[v] = (mode & 4) ? t : ACC.ld(4LL * b.z + v) + t;
+                    }
+                    if (!(mode & 8)) {
+                        for (int v = 0; v < 4; v++) ACC.st(4LL * b.z + v, amp[v]);
+                        break;
+                    }
+                }
+                const int end = b.x + b.y;
+                for (int s = b.x; s < end; s++) {
+                    const int e = __ldg(scat + s);
+                    double *jc = jr + (long long)(e >> 2) * R;
+                    for (int v = 0; v < 4; v++) {
+                        const cx t = unit_times(e, amp[v]);
+                        jc[2 * v * nipad] += t.r;
+                        jc[(2 * v + 1) * nipad] += t.i;
+                    }
+                }
+                break;
+            }
+            default:
+                break;
+        }
+    }
+}
+
+template <int NG>
+__global__ void __launch_bounds__(BIG_BLOCK)
+    k_sigmakin_big(const double *__restrict__ mom, long long nitem, int nunits,
+                   const int *__restrict__ units, const int4 *__restrict__ ops, int nops,
+                   const int *__restrict__ scat, double mt, double wt, double2 *__restrict__ scratch,
+                   long long T, int nsg, int nsf, double *__restrict__ jrow, long long R,
+                   long long nipad) {
+    constexpr int NPAR = NG + 2;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    const Strided WG{scratch + t, T};
+    const Strided WF{scratch + 4LL * nsg * T + t, T};
+    const Strided ACC{scratch + (4LL * nsg + 8LL * nsf) * T + t, T};
+    for (long long item = t; item < nitem; item += T) {
+        const long long e = item / nunits;
+        const int u = __ldg(units + (item - e * nunits));
+        Kin<NG> k;
+        kinematics<NG>(k, mom + e * (NPAR * 4), mt, wt);
+        run_item<NG>(k, u >> 4, ops, nops, scat, mt, WG, WF, ACC, jrow + item, R, nipad);
+    }
+}
+
+// Colour sum of every row r over the block upper triangle:
+// qpart[I * R + r] = sum_{n in tile I} V_rn Z_rn,  Z_rn = sum_{k >= 64 I} Cb_nk V_rk,
+// with V_rk = jrow[k * R + r] and cbT[k * np + n] = Cb_nk.  Tile 64 rows x 64
+// colours, 256 threads with 4 x 4 results each (thread (tx, ty): colours
+// tx + 16 j, rows ty + 16 i), k in chunks of 16 through shared memory.
+__global__ void __launch_bounds__(256)
+    k_colour_big(const double *__restrict__ jrow, long long R, const double *__restrict__ cbT,
+                 int np, double *__restrict__ qpart) {
+    __shared__ double As[CK][RT];
+    __shared__ double Bs[CK][CT];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const long long r0 = (long long)blockIdx.x * RT;
+    const int n0 = blockIdx.y * CT;
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
+    for (int k0 = n0; k0 < np; k0 += CK) {
+#pragma unroll
+        for (int q = 0; q < (CK * RT) / 256; q++) {
+            const int idx = tid + 256 * q;
+            const int kk = idx / RT, rr = idx % RT;
+            As[kk][rr] = jrow[(long long)(k0 + kk) * R + r0 + rr];
+            Bs[kk][rr] = cbT[(long long)(k0 + kk) * np + n0 + rr];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < CK; kk++) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; j++) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const long long r = r0 + ty + 16 * i;
+        double s = 0.0;
+#pragma unroll
+        for (int j = 0; j < 4; j++) s = fma(jrow[(long long)(n0 + tx + 16 * j) * R + r], acc[i][j], s);
+        for (int off = 8; off >= 1; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (tx == 0) qpart[(long long)blockIdx.y * R + r] = s;
+    }
+}
+
+// Per event: sum over its items (units), good helicity combinations,
+// real/imaginary rows and colour tiles, in that fixed order.
+template <int NG>
+__global__ void k_event_sum_big(const double *__restrict__ qpart, long long R, int ntile,
+                                long long nipad, const int *__restrict__ units, int nunits,
+                                long long nevt, double factor, double *__restrict__ me,
+                                double *__restrict__ me_hel) {
+    constexpr int NPAR = NG + 2;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nevt) return;
+    double tot = 0.0;
+    for (int iu = 0; iu < nunits; iu++) {
+        const long long item = e * nunits + iu;
+        const int u = __ldg(units + iu);
+        for (int v = 0; v < 4; v++) {
+            if (!((u >> v) & 1)) continue;
+            double mh = 0.0;
+            for (int ri = 0; ri < 2; ri++) {
+                const long long r = (2 * v + ri) * nipad + item;
+                for (int I = 0; I < ntile; I++) mh += qpart[(long long)I * R + r];
+            }
+            tot += mh;
+            if (me_hel) me_hel[e * (1LL << NPAR) + helicity_index<NG>(u >> 4, v >> 1, v & 1)] = mh * factor;
+        }
+    }
+    if (me) me[e] = tot * factor;
+}
+
+// Block upper triangle of D*C, transposed for the k-major tiles:
+// cbT[k * np + n] = w * C_nk with w = 1 on the 64 x 64 diagonal blocks, 2
+// above them, 0 below and in the padding.  C_nk = row[rank(r)] with r_i the
+// position in ordering n of the i-th label of ordering k (the summed colour
+// labels are dummies, so only the relative ordering matters).
+template <int NG>
+__global__ void k_build_cbig(const long long *__restrict__ row, const signed char *__restrict__ perm,
+                             int nc, int np, double *__restrict__ cbT) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)np * np) return;
+    const int k = (int)(idx / np), n = (int)(idx % np);
+    const int bi = n / CT, bj = k / CT;
+    double val = 0.0;
+    if (n < nc && k < nc && bj >= bi) {
+        int pos[NG];
+        for (int a = 0; a < NG; a++) pos[perm[n * NG + a]] = a;
+        long long rank = 0;
+        unsigned used = 0;
+        for (int i = 0; i < NG; i++) {
+            const int ri = pos[perm[k * NG + i]];
+            const int smaller = __popc(~used & ((1u << ri) - 1u));
+            rank = rank * (NG - i) + smaller;
+            used |= 1u << ri;
+        }
+        val = (double)row[rank] * (bj > bi ? 2.0 : 1.0);
+    }
+    cbT[idx] = val;
+}
+
+}  // namespace
+
+int mg_big_ngluon() { return BIG_NG; }
+
+size_t mg_big_state_bytes(int nslot, int nslot_top, int nslot_acc) {
+    return (size_t)(4LL * nslot + 8LL * nslot_top + 4LL * nslot_acc) * sizeof(double2);
+}
+
+int mg_big_block() { return BIG_BLOCK; }
+
+cudaError_t mg_launch_build_cbig(const long long *row, const signed char *perm, int nc, int np,
+                                 double *cbT, cudaStream_t stream) {
+    if (np % CT || np < nc) return cudaErrorInvalidValue;
+    const long long n = (long long)np * np;
+    mg_note_launch();
+    k_build_cbig<BIG_NG><<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(row, perm, nc, np, cbT);
+    return cudaGetLastError();
+}
+
+cudaError_t mg_launch_sigmakin_big(const mg_dev_proc &dp, const double *mom, long long nitem,
+                                   const int *units, int nunits, int nsg, int nsf, double2 *scratch,
+                                   long long T, double *jrow, long long R, long long nipad,
+                                   cudaStream_t stream) {
+    if (nitem <= 0) return cudaSuccess;
+    if (T <= 0 || T % BIG_BLOCK || R != 8 * nipad || nipad < nitem) return cudaErrorInvalidValue;
+    mg_note_launch();
+    k_sigmakin_big<BIG_NG><<<(unsigned)(T / BIG_BLOCK), BIG_BLOCK, 0, stream>>>(
+        mom, nitem, nunits, units, reinterpret_cast<const int4 *>(dp.ops), dp.nops, dp.scat, dp.mt,
+        dp.wt, scratch, T, nsg, nsf, jrow, R, nipad);
+    return cudaGetLastError();
+}
+
+cudaError_t mg_launch_colour_big(const double *jrow, long long R, const double *cbT, int np,
+                                 double *qpart, cudaStream_t stream) {
+    if (R <= 0) return cudaSuccess;
+    if (R % RT || np % CT) return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)(R / RT), (unsigned)(np / CT));
+    mg_note_launch();
+    k_colour_big<<<grid, 256, 0, stream>>>(jrow, R, cbT, np, qpart);
+    return cudaGetLastError();
+}
+
+cudaError_t mg_launch_event_sum_big(const double *qpart, long long R, int ntile, long long nipad,
+                                    const int *units, int nunits, long long nevt, double factor,
+                                    double *me, double *me_hel, cudaStream_t stream) {
+    if (nevt <= 0) return cudaSuccess;
+    mg_note_launch();
+    k_event_sum_big<BIG_NG><<<(unsigned)((nevt + 127) / 128), 128, 0, stream>>>(
+        qpart, R, ntile, nipad, units, nunits, nevt, factor, me, me_hel);
+    return cudaGetLastError();
+}

@@ -24,7 +24,9 @@ typedef struct {
     double flops_colour;     // algorithmic FP64 flops per helicity (colour sum)
     const int32_t *ops;      // [nops][8]
     const int32_t *scat;     // [nscat]
-    const int32_t *chat;     // [ncolor][ncolor], D * C
+    const int32_t *chat;     // [ncolor][ncolor], D * C (NULL for table-file processes)
+    const int64_t *crow;     // table-file processes: D * C by relative ordering [ncolor]
+    const int8_t *cperm;     // table-file processes: flow orderings [ncolor][ngluon]
 } mg_proc_table;
 
 const mg_proc_table *mg_tables(int *count);
@@ -116,6 +118,21 @@ cudaError_t mg_launch_colorsum_tc(const __nv_bfloat16 *jbuf, long long ncols_all
 cudaError_t mg_launch_event_sum(const double *part, long long nevt, int per_event, double factor,
                                 double *me, cudaStream_t stream);
 size_t mg_tc_smem_bytes(int kp, int np);
+// processes with their state in HBM (mg_big.cu)
+int mg_big_ngluon();
+int mg_big_block();
+size_t mg_big_state_bytes(int nslot, int nslot_top, int nslot_acc);
+cudaError_t mg_launch_build_cbig(const long long *row, const signed char *perm, int nc, int np,
+                                 double *cbT, cudaStream_t stream);
+cudaError_t mg_launch_sigmakin_big(const mg_dev_proc &dp, const double *mom, long long nitem,
+                                   const int *units, int nunits, int nsg, int nsf, double2 *scratch,
+                                   long long T, double *jrow, long long R, long long nipad,
+                                   cudaStream_t stream);
+cudaError_t mg_launch_colour_big(const double *jrow, long long R, const double *cbT, int np,
+                                 double *qpart, cudaStream_t stream);
+cudaError_t mg_launch_event_sum_big(const double *qpart, long long R, int ntile, long long nipad,
+                                    const int *units, int nunits, long long nevt, double factor,
+                                    double *me, double *me_hel, cudaStream_t stream);
 // counts a kernel launch of the library (measurement; replays of captured
 // graphs are not launches of this kind and are not counted)
 void mg_note_launch();

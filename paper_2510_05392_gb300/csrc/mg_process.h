@@ -17,7 +17,7 @@ struct mg_process {
     int *d_units;        // work units (device): gluon config << 4 | top-helicity mask
     int nunits;
     int ngood;           // -1 until filtered
-    uint8_t mask[256];
+    uint8_t mask[512];
     int tpe, block;      // launch shape
     double factor;
     // mixed precision: tensor-core colour sum (precision == MG_MIXED_BF16)
@@ -39,10 +39,24 @@ struct mg_process {
     cudaEvent_t *tev;            // [2 * tcap]
     int *tkind;                  // [tcap] MG_KT_* of each recorded launch
     int tcap, tn, tdropped;
+    // processes loaded from a table file, run with their state in HBM (mg_big.cu)
+    int big;
+    mg_proc_table *own_tab;      // host tables owned by the process
+    long long *d_crow;           // device [ncolor] D*C by relative ordering
+    signed char *d_cperm;        // device [ncolor][ngluon] flow orderings
+    double *d_cbig;              // device [np][np] block upper triangle of D*C, k-major
+    int big_np;                  // colours padded to the 64-colour tile
+    double2 *d_scratch;          // per-thread wavefunction state, slot-major
+    long long scratch_threads;   // threads the scratch holds
+    long long big_threads;       // threads per launch (0: default)
+    double *d_jrow;              // FP64 jamp rows of one chunk, colour-major
+    long long jrow_items;        // items (padded) the row buffer holds
+    double *d_qpart;             // per-tile colour sums of one chunk
+    long long qpart_len;
 };
 
 // kinds of timed launches
-enum { MG_KT_DIAGRAM = 0, MG_KT_COLOUR_TC = 1, MG_KT_EVENT_SUM = 2, MG_KT_NKIND = 3 };
+enum { MG_KT_DIAGRAM = 0, MG_KT_COLOUR = 1, MG_KT_EVENT_SUM = 2, MG_KT_NKIND = 3 };
 
 // Timing of one launch: mg_timer_begin records the start event (returns the
 // slot, or -1 when timing is off or the pool is full), mg_timer_end the stop.

@@ -1,0 +1,90 @@
+"""GPU: g g -> t t~ + 5 g (2 -> 7, 5040 colour flows), run with its state in
+HBM from the process compiler's table file, against the CPU oracle
+(Berends-Giele colour-ordered amplitudes and the exact colour matrix).
+
+The table file is generated on first use (a few minutes); the oracle takes a
+few seconds per event on the host cores."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_05392_gb300 import binding
+from paper_2510_05392_gb300 import phasespace as ps
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PROC = "g g > t t~ g g g g g"
+RTOL = 1e-9
+
+
+def _events(n, seed):
+    return ps.generate(n, 5, 2000.0, seed, ptmin=20.0, drmin=0.4)
+
+
+@pytest.fixture(scope="module")
+def big():
+    return binding.Process(PROC, hel_mode=binding.MG_HEL_ALL)
+
+
+@pytest.fixture(scope="module")
+def events():
+    mom = _events(3, 424242)
+    return mom, oracle.me(mom, per_helicity=True)
+
+
+def test_info(big):
+    i = big.info()
+    assert (i.npar, i.ngluon, i.ncolor, i.nhel, i.ngood) == (9, 7, 5040, 512, 512)
+
+
+def test_me_and_per_helicity_match_oracle(big, events):
+    mom, (ref, ref_h) = events
+    md = torch.from_numpy(mom).cuda()
+    out = torch.empty(len(mom), dtype=torch.float64, device="cuda")
+    out_h = torch.empty((len(mom), 512), dtype=torch.float64, device="cuda")
+    big.sigmakin(md, out)
+    single = out.clone()
+    big.sigmakin_hel(md, out, out_h)
+    torch.cuda.synchronize()
+    got, got_h = out.cpu().numpy(), out_h.cpu().numpy()
+    assert np.abs(got / ref - 1).max() <= RTOL
+    assert np.array_equal(single.cpu().numpy(), got)       # deterministic
+    scale = ref_h.max(axis=1, keepdims=True)
+    assert np.abs(got_h - ref_h).max() <= RTOL * scale.min()
+    np.testing.assert_allclose(got_h.sum(axis=1), got, rtol=1e-13)
+
+
+def test_chunks_and_ragged_sizes(big, events):
+    """One event, then the three events again: same values whatever the
+    batch (the items of a launch are independent)."""
+    mom, (ref, _) = events
+    md = torch.from_numpy(mom).cuda()
+    one = torch.empty(1, dtype=torch.float64, device="cuda")
+    big.sigmakin(md[1:2], one)
+    torch.cuda.synchronize()
+    assert abs(one.item() / ref[1] - 1) <= RTOL
+
+
+def test_filter_keeps_every_helicity(events):
+    mom, (_, ref_h) = events
+    p = binding.Process(PROC)
+    n = p.filter_helicities(torch.from_numpy(mom[:2]).cuda())
+    expect = oracle.good_helicity_mask(mom[:2])
+    assert n == int(expect.sum())
+    assert np.array_equal(p.helicity_mask().astype(bool), expect.astype(bool))
+
+
+def test_colour_matrix_matches_oracle(big):
+    got, d = big.color_matrix()
+    ref, D, _ = oracle.color_data(7)
+    assert d == D
+    assert np.array_equal(got, ref)
+
+
+def test_unsupported_paths(big):
+    with pytest.raises(binding.MGError):
+        binding.Process(PROC, precision=binding.MG_MIXED_BF16)
+    mom = torch.from_numpy(_events(1, 5)).cuda()
+    with pytest.raises(binding.MGError):
+        big.sigmakin_ex(mom, torch.empty(1, dtype=torch.float64, device="cuda"))

@@ -26,10 +26,10 @@ def test_kernel_times_count_every_launch(precision):
     ms, n = kt["diagram"]
     assert n == 3 and ms > 0.0
     if precision == binding.MG_MIXED_BF16:
-        assert kt["colour_tc"][1] == 3 and kt["colour_tc"][0] > 0.0
+        assert kt["colour"][1] == 3 and kt["colour"][0] > 0.0
         assert kt["event_sum"][1] == 3
     else:
-        assert kt["colour_tc"][1] == 0 and kt["event_sum"][1] == 0
+        assert kt["colour"][1] == 0 and kt["event_sum"][1] == 0
     # after a reset nothing is reported; timing off records nothing
     assert p.kernel_times()["diagram"][1] == 0
     p.set_kernel_timing(0)

@@ -42,10 +42,10 @@ WORKLOADS = {
     "ggtt_16384": ("g g > t t~", 0, 16384, 1000.0, False, 20251005 + 1),
     "ggttggg_262144": ("g g > t t~ g g g", 3, 262144, 1500.0, True, 20251005 + 3),
     # 2 -> 7 (5040 flows): state in HBM, FP64 colour sum kernel of its own
-    "ggttggggg_256": ("g g > t t~ g g g g g", 5, 256, 2000.0, True, 20251005 + 6),
+    "ggttggggg_512": ("g g > t t~ g g g g g", 5, 512, 2000.0, True, 20251005 + 6),
 }
 # oracle events per CPU sample where one event takes seconds on the host
-CPU_SAMPLE_CAP = {"ggttggggg_256": 4}
+CPU_SAMPLE_CAP = {"ggttggggg_512": 4}
 TEST_SEED = 12345  # helicity-filter test events
 
 

@@ -99,7 +99,7 @@ int mg_process_create(const char *process, const mg_params *params, mg_process *
  * program, jamp scatter, colour row by relative ordering, flow orderings).
  * Every index of the program is checked against its pools before anything
  * reaches the device; a damaged or foreign file gives MG_ERR_BAD_PROCESS.
- * Runs with its wavefunction state in HBM (about 1.9 MB per thread, two
+ * Runs with its wavefunction state in HBM (about 1.9 MB per thread, three
  * 128-thread blocks per SM while half the free memory holds them) and an
  * FP64 colour sum over the block upper triangle of the 5040 x 5040 colour
  * matrix (built on the device, 203 MB).  FP64 only (MG_MIXED_BF16:

@@ -171,7 +171,7 @@ int setup_mixed(mg_process *p) {
 
 // ---------------------------------------------------------------------------
 // Processes loaded from a table file and run with their state in HBM
-// (mg_big.cu): chunks of events whose FP64 jamp rows fit 12 GiB; per chunk
+// (mg_big.cu): chunks of events whose FP64 jamp rows fit 24 GiB; per chunk
 // the rows are cleared, the diagram kernel accumulates the jamps into them,
 // the colour-sum kernel forms every row's quadratic form per 64-colour tile
 // and the event sum adds them up.
@@ -187,15 +187,16 @@ int sigmakin_big(mg_process *p, const double *mom, int64_t nevt, double *me, dou
     }
     const long long np = p->big_np;
     const int ntile = (int)(np / 64);
-    const long long row_limit = (12LL << 30) / (np * 8);      // rows of 12 GiB
+    const long long row_limit = (24LL << 30) / (np * 8);      // rows of 24 GiB
     long long ev_chunk = row_limit / (8LL * nu);
     if (ev_chunk < 1) ev_chunk = 1;
     if (ev_chunk > nevt) ev_chunk = nevt;
     const long long nipad_max = (ev_chunk * nu + 7) / 8 * 8;
-    // threads: two 128-thread CTAs per SM while the device has room for their
-    // state, never more than the items of a chunk
-    int nsm = 0;
+    // threads: the resident blocks of every SM while the device has room for
+    // their state, never more than the items of a chunk
+    int nsm = 0, occ = 0;
     MG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device));
+    if (mg_big_blocks_per_sm(&occ) != 0 || occ < 1) return MG_ERR_CUDA;
     const int blk = mg_big_block();
     const size_t state = mg_big_state_bytes(t->nslot, t->nslot_top, t->nslot_acc);
     long long T = p->big_threads;
@@ -203,11 +204,13 @@ int sigmakin_big(mg_process *p, const double *mom, int64_t nevt, double *me, dou
         size_t freeb = 0, totalb = 0;
         MG_CUDA(cudaMemGetInfo(&freeb, &totalb));
         const long long have = p->scratch_threads;
-        T = 2LL * nsm * blk;
+        T = (long long)occ * nsm * blk;
         while (T > blk && T > have && (size_t)(T - have) * state > freeb / 2) T -= blk;
     }
-    const long long need = (nipad_max + blk - 1) / blk * blk;
-    if (T > need) T = need;
+    // every thread holds one item (seconds of work) at a time: spread the
+    // items of a full chunk evenly over whole waves of threads
+    const long long waves = (ev_chunk * nu + T - 1) / T;
+    T = ((ev_chunk * nu + waves - 1) / waves + blk - 1) / blk * blk;
     if (T > p->scratch_threads) {
         cudaFree(p->d_scratch);
         p->d_scratch = nullptr;

@@ -40,6 +40,7 @@ constexpr int BIG_BLOCK = 128;
 constexpr int CT = 64;   // colour tile (n and k) of the quadratic form
 constexpr int CK = 16;   // k chunk per shared-memory stage
 constexpr int RT = 64;   // rows per tile
+constexpr int SCAT_BATCH = 2;   // jamp updates loaded together
 
 // slot-major, thread-interleaved state; p already offset by the thread
 struct Strided {
@@ -60,6 +61,53 @@ struct Strided {
     }
 };
 
+__device__ __forceinline__ void prefetch_l2(const double2 *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// slot s of a pool with `per` elements per slot
+__device__ __forceinline__ void prefetch_slot(const Strided &P, int per, int s) {
+    for (int m = 0; m < per; m++) prefetch_l2(P.p + (long long)(per * s + m) * P.T);
+}
+
+// The wavefunctions an op will read (same field meaning as run_item).
+__device__ __forceinline__ void prefetch_inputs(const int4 &a, const int4 &b, const Strided &WG,
+                                                const Strided &WF, const Strided &ACC) {
+    switch (a.x) {
+        case MG_OP_V3:
+            prefetch_slot(WG, 4, a.z);
+            prefetch_slot(WG, 4, a.w);
+            break;
+        case MG_OP_V4:
+            prefetch_slot(WG, 4, b.x);
+            prefetch_slot(WG, 4, b.y);
+            prefetch_slot(WG, 4, b.z);
+            break;
+        case MG_OP_FPRE:
+        case MG_OP_FSUF:
+        case MG_OP_XROW:
+            prefetch_slot(WG, 4, a.w);
+            prefetch_slot(WF, 8, a.z);
+            break;
+        case MG_OP_YCOL:
+            prefetch_slot(WG, 4, a.z);
+            prefetch_slot(WF, 8, a.w);
+            break;
+        case MG_OP_BIL:
+        case MG_OP_AMP_SS:
+            prefetch_slot(WF, 8, a.z);
+            prefetch_slot(WF, 8, a.w);
+            if (a.x == MG_OP_AMP_SS && b.z >= 0 && !(b.w & 4)) prefetch_slot(ACC, 4, b.z);
+            break;
+        case MG_OP_AMP_VV:
+            prefetch_slot(WG, 4, a.w);
+            if (b.z >= 0 && !(b.w & 4)) prefetch_slot(ACC, 4, b.z);
+            break;
+        default:
+            break;
+    }
+}
+
 // The program of one item (same ops and semantics as the local-memory
 // interpreter of mg_kernels.cu): pools G (slot s, component m: 4 s + m),
 // F (slot s, variant v, component m: 8 s + 4 v + m), A (slot s, variant v:
@@ -71,9 +119,16 @@ __device__ void run_item(const Kin<NG> &k, int g, const int4 *__restrict__ ops, 
                          const Strided &WF, const Strided &ACC, double *__restrict__ jr, long long R,
                          long long nipad) {
     cx G0[4][4];
+    int4 an = __ldg(ops), bn = __ldg(ops + 1);
     for (int i = 0; i < nops; i++) {
-        const int4 a = __ldg(ops + 2 * i);
-        const int4 b = __ldg(ops + 2 * i + 1);
+        // this op's record was loaded one op ago; start the next record's
+        // load and pull the next op's inputs towards L2 while this one runs
+        const int4 a = an, b = bn;
+        if (i + 1 < nops) {
+            an = __ldg(ops + 2 * (i + 1));
+            bn = __ldg(ops + 2 * (i + 1) + 1);
+            prefetch_inputs(an, bn, WG, WF, ACC);
+        }
         switch (a.x) {
             case MG_OP_EXT_G: {
                 const int gi = (a.z < 2) ? a.z : a.z - 2;
@@ -188,15 +243,33 @@ __device__ void run_item(const Kin<NG> &k, int g, const int4 *__restrict__ ops, 
                         break;
                     }
                 }
+                // jamp updates in batches: every old value of a batch is
+                // loaded before any is stored (the flows of one scatter list
+                // are distinct), so the batch waits for memory once
                 const int end = b.x + b.y;
-                for (int s = b.x; s < end; s++) {
-                    const int e = __ldg(scat + s);
-                    double *jc = jr + (long long)(e >> 2) * R;
-                    for (int v = 0; v < 4; v++) {
-                        const cx t = unit_times(e, amp[v]);
-                        jc[2 * v * nipad] += t.r;
-                        jc[(2 * v + 1) * nipad] += t.i;
-                    }
+                for (int s0 = b.x; s0 < end; s0 += SCAT_BATCH) {
+                    int ev[SCAT_BATCH];
+                    double old[SCAT_BATCH][8];
+#pragma unroll
+                    for (int q = 0; q < SCAT_BATCH; q++) ev[q] = (s0 + q < end) ? __ldg(scat + s0 + q) : -1;
+#pragma unroll
+                    for (int q = 0; q < SCAT_BATCH; q++)
+                        if (ev[q] >= 0) {
+                            const double *jc = jr + (long long)(ev[q] >> 2) * R;
+#pragma unroll
+                            for (int w = 0; w < 8; w++) old[q][w] = jc[w * nipad];
+                        }
+#pragma unroll
+                    for (int q = 0; q < SCAT_BATCH; q++)
+                        if (ev[q] >= 0) {
+                            double *jc = jr + (long long)(ev[q] >> 2) * R;
+#pragma unroll
+                            for (int v = 0; v < 4; v++) {
+                                const cx t = unit_times(ev[q], amp[v]);
+                                jc[2 * v * nipad] = old[q][2 * v] + t.r;
+                                jc[(2 * v + 1) * nipad] = old[q][2 * v + 1] + t.i;
+                            }
+                        }
                 }
                 break;
             }
@@ -207,7 +280,7 @@ __device__ void run_item(const Kin<NG> &k, int g, const int4 *__restrict__ ops, 
 }
 
 template <int NG>
-__global__ void __launch_bounds__(BIG_BLOCK)
+__global__ void __launch_bounds__(BIG_BLOCK, 3)   // 168 registers: three blocks per SM
     k_sigmakin_big(const double *__restrict__ mom, long long nitem, int nunits,
                    const int *__restrict__ units, const int4 *__restrict__ ops, int nops,
                    const int *__restrict__ scat, double mt, double wt, double2 *__restrict__ scratch,
@@ -346,6 +419,13 @@ size_t mg_big_state_bytes(int nslot, int nslot_top, int nslot_acc) {
 }
 
 int mg_big_block() { return BIG_BLOCK; }
+
+int mg_big_blocks_per_sm(int *out) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_sigmakin_big<BIG_NG>, BIG_BLOCK, 0) ==
+                   cudaSuccess
+               ? 0
+               : -1;
+}
 
 cudaError_t mg_launch_build_cbig(const long long *row, const signed char *perm, int nc, int np,
                                  double *cbT, cudaStream_t stream) {

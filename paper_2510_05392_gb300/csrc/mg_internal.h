@@ -121,6 +121,7 @@ size_t mg_tc_smem_bytes(int kp, int np);
 // processes with their state in HBM (mg_big.cu)
 int mg_big_ngluon();
 int mg_big_block();
+int mg_big_blocks_per_sm(int *out);
 size_t mg_big_state_bytes(int nslot, int nslot_top, int nslot_acc);
 cudaError_t mg_launch_build_cbig(const long long *row, const signed char *perm, int nc, int np,
                                  double *cbT, cudaStream_t stream);

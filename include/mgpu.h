@@ -102,8 +102,10 @@ int mg_process_create(const char *process, const mg_params *params, mg_process *
  * Runs with its wavefunction state in HBM (about 1.9 MB per thread, three
  * 128-thread blocks per SM while half the free memory holds them) and an
  * FP64 colour sum over the block upper triangle of the 5040 x 5040 colour
- * matrix (built on the device, 203 MB).  FP64 only (MG_MIXED_BF16:
- * MG_ERR_UNSUPPORTED); mg_sigmakin, mg_sigmakin_hel, mg_filter_helicities,
+ * matrix (built on the device, 203 MB); with MG_MIXED_BF16 the colour sum
+ * runs on the tensor cores instead (jamps as three BF16 pieces, D*C as
+ * C_hi + C_lo, FP32 accumulation per 128-colour block, blocks added in FP64;
+ * relative error about 1e-6).  mg_sigmakin, mg_sigmakin_hel, mg_filter_helicities,
  * mg_color_matrix and the timing hooks work as for the other processes;
  * mg_sigmakin_ex, the batch calls and mg_filter_helicities_noalloc return
  * MG_ERR_UNSUPPORTED. */

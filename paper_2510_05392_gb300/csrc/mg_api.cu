@@ -186,12 +186,15 @@ int sigmakin_big(mg_process *p, const double *mom, int64_t nevt, double *me, dou
         return MG_OK;
     }
     const long long np = p->big_np;
-    const int ntile = (int)(np / 64);
+    const bool mixed = p->par.precision == MG_MIXED_BF16;
+    // FP64: one partial per 64-colour tile; mixed: per half of a 128-colour tile
+    const int ntile = mixed ? 2 * p->kp / 128 : (int)(np / 64);
+    const int ipad = mixed ? 16 : 8;   // items per padding unit: rows in whole 128-row tiles
     const long long row_limit = (24LL << 30) / (np * 8);      // rows of 24 GiB
     long long ev_chunk = row_limit / (8LL * nu);
     if (ev_chunk < 1) ev_chunk = 1;
     if (ev_chunk > nevt) ev_chunk = nevt;
-    const long long nipad_max = (ev_chunk * nu + 7) / 8 * 8;
+    const long long nipad_max = (ev_chunk * nu + ipad - 1) / ipad * ipad;
     // threads: the resident blocks of every SM while the device has room for
     // their state, never more than the items of a chunk
     int nsm = 0, occ = 0;
@@ -227,6 +230,11 @@ int sigmakin_big(mg_process *p, const double *mom, int64_t nevt, double *me, dou
         p->jrow_items = 0;
         cudaError_t e = cudaMalloc(&p->d_jrow, sizeof(double) * np * 8 * nipad_max);
         if (e == cudaSuccess) e = cudaMalloc(&p->d_qpart, sizeof(double) * ntile * 8 * nipad_max);
+        if (e == cudaSuccess && mixed) {
+            cudaFree(p->d_jbuf);
+            p->d_jbuf = nullptr;
+            e = cudaMalloc(&p->d_jbuf, sizeof(__nv_bfloat16) * 3 * p->kp * 8 * nipad_max);
+        }
         if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? MG_ERR_NO_MEMORY : cuda_fail(e);
         p->jrow_items = nipad_max;
     }
@@ -234,7 +242,7 @@ int sigmakin_big(mg_process *p, const double *mom, int64_t nevt, double *me, dou
     for (long long e0 = 0; e0 < nevt; e0 += ev_chunk) {
         const long long n = (nevt - e0 < ev_chunk) ? nevt - e0 : ev_chunk;
         const long long nitem = n * nu;
-        const long long nip = (nitem + 7) / 8 * 8;
+        const long long nip = (nitem + ipad - 1) / ipad * ipad;
         const long long R = 8 * nip;
         MG_CUDA(cudaMemsetAsync(p->d_jrow, 0, sizeof(double) * np * R, s));
         int slot = mg_timer_begin(p, s, MG_KT_DIAGRAM);
@@ -242,7 +250,13 @@ int sigmakin_big(mg_process *p, const double *mom, int64_t nevt, double *me, dou
                                        t->nslot_top, p->d_scratch, T, p->d_jrow, R, nip, s));
         mg_timer_end(p, s, slot);
         slot = mg_timer_begin(p, s, MG_KT_COLOUR);
-        MG_CUDA(mg_launch_colour_big(p->d_jrow, R, p->d_cbig, (int)np, p->d_qpart, s));
+        if (mixed) {
+            MG_CUDA(mg_launch_rows_to_bf16(p->d_jrow, R, (int)np, p->kp, p->d_jbuf, s));
+            MG_CUDA(mg_launch_colorsum_tc_big(p->d_jbuf, R, p->kp, p->d_cmat, p->np, p->debug_extra_tx,
+                                              p->d_qpart, p->d_err, s));
+        } else {
+            MG_CUDA(mg_launch_colour_big(p->d_jrow, R, p->d_cbig, (int)np, p->d_qpart, s));
+        }
         mg_timer_end(p, s, slot);
         slot = mg_timer_begin(p, s, MG_KT_EVENT_SUM);
         MG_CUDA(mg_launch_event_sum_big(p->d_qpart, R, ntile, nip, p->d_units, nu, n, p->factor,
@@ -498,10 +512,24 @@ int mg_process_create_from_tables(const char *path, const mg_params *params, mg_
     if (params) par = *params;
     if (!(par.mt > 0.0) || !(par.wt >= 0.0) || !(par.alphas > 0.0)) return MG_ERR_BAD_ARG;
     if (par.hel_mode != MG_HEL_FILTERED && par.hel_mode != MG_HEL_ALL) return MG_ERR_BAD_ARG;
-    if (par.precision != MG_FP64) return MG_ERR_UNSUPPORTED;
+    if (par.precision != MG_FP64 && par.precision != MG_MIXED_BF16) return MG_ERR_BAD_ARG;
     int st = MG_OK;
     mg_proc_table *t = read_table_file(path, &st);
     if (!t) return st;
+    if (par.precision == MG_MIXED_BF16)   // D*C = C_hi + C_lo must be exact in BF16
+        for (int i = 0; i < t->ncolor; i++) {
+            const float c = (float)t->crow[i];
+            const __nv_bfloat16 hi = __float2bfloat16_rn(c);
+            const __nv_bfloat16 lo = __float2bfloat16_rn(c - __bfloat162float(hi));
+            if ((double)__bfloat162float(hi) + (double)__bfloat162float(lo) != (double)t->crow[i]) {
+                free((void *)t->ops);
+                free((void *)t->scat);
+                free((void *)t->crow);
+                free((void *)t->cperm);
+                free(t);
+                return MG_ERR_UNSUPPORTED;
+            }
+        }
     mg_process *p = (mg_process *)calloc(1, sizeof(mg_process));
     if (!p) {
         free((void *)t->ops);
@@ -523,6 +551,9 @@ int mg_process_create_from_tables(const char *path, const mg_params *params, mg_
     p->factor = pow(gs, 2 * t->ngluon) / (t->iden * (double)t->denom);
     p->big_np = 64 * ((t->ncolor + 63) / 64);
     const size_t np = (size_t)p->big_np;
+    const bool mixed = par.precision == MG_MIXED_BF16;
+    p->kp = mixed ? 128 * ((t->ncolor + 127) / 128) : 0;
+    p->np = p->kp;
     cudaError_t e = cudaGetDevice(&p->device);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_ops, sizeof(int32_t) * 8 * t->nops);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_scat, sizeof(int32_t) * (t->nscat > 0 ? t->nscat : 1));
@@ -530,14 +561,19 @@ int mg_process_create_from_tables(const char *path, const mg_params *params, mg_
     if (e == cudaSuccess) e = cudaMalloc(&p->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&p->d_crow, sizeof(long long) * t->ncolor);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_cperm, (size_t)t->ncolor * t->ngluon);
-    if (e == cudaSuccess) e = cudaMalloc(&p->d_cbig, sizeof(double) * np * np);
+    if (e == cudaSuccess && !mixed) e = cudaMalloc(&p->d_cbig, sizeof(double) * np * np);
+    if (e == cudaSuccess && mixed)
+        e = cudaMalloc(&p->d_cmat, sizeof(__nv_bfloat16) * 2 * (size_t)p->kp * p->kp);
     if (e == cudaSuccess) e = cudaMemcpy(p->d_ops, t->ops, sizeof(int32_t) * 8 * t->nops, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && t->nscat > 0)
         e = cudaMemcpy(p->d_scat, t->scat, sizeof(int32_t) * t->nscat, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpy(p->d_crow, t->crow, sizeof(long long) * t->ncolor, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->d_cperm, t->cperm, (size_t)t->ncolor * t->ngluon, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = mg_launch_build_cbig(p->d_crow, p->d_cperm, t->ncolor, (int)np, p->d_cbig, 0);
+    if (e == cudaSuccess && !mixed)
+        e = mg_launch_build_cbig(p->d_crow, p->d_cperm, t->ncolor, (int)np, p->d_cbig, 0);
+    if (e == cudaSuccess && mixed)
+        e = mg_launch_build_cmat_bf16(p->d_crow, p->d_cperm, t->ncolor, p->kp, p->d_cmat, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         free_proc(p);

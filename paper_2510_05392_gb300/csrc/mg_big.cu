@@ -24,6 +24,7 @@
 //   k_event_sum_big per event, the sum over its items, good helicity
 //                   combinations, real/imaginary rows and tiles in a fixed
 //                   order (and |M_h|^2 per helicity for the filter).
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -410,6 +411,63 @@ __global__ void k_build_cbig(const long long *__restrict__ row, const signed cha
     cbT[idx] = val;
 }
 
+// Mixed precision: FP64 colour-major rows jrow[c * R + r] (c < nsrc) to the
+// tensor-core rows jb[r * 3 kp + s * kp + c] (s = hi, mid, lo: the value
+// rounded to FP32, then split twice into BF16), colours >= nsrc zero.
+// Tiles of 64 rows x 64 colours through shared memory (reads coalesced along
+// rows, writes along colours).
+__global__ void __launch_bounds__(256)
+    k_rows_to_bf16(const double *__restrict__ jrow, long long R, int nsrc, int kp,
+                   __nv_bfloat16 *__restrict__ jb) {
+    __shared__ double tile[64][65];
+    const long long r0 = (long long)blockIdx.x * 64;
+    const int c0 = blockIdx.y * 64;
+    const int tid = threadIdx.x;
+    for (int q = tid; q < 64 * 64; q += 256) {
+        const int cc = q / 64, rr = q % 64;
+        tile[cc][rr] = (c0 + cc < nsrc) ? jrow[(long long)(c0 + cc) * R + r0 + rr] : 0.0;
+    }
+    __syncthreads();
+    for (int q = tid; q < 64 * 64; q += 256) {
+        const int rr = q / 64, cc = q % 64;
+        const float f = __double2float_rn(tile[cc][rr]);
+        const __nv_bfloat16 hi = __float2bfloat16_rn(f);
+        const float r1 = f - __bfloat162float(hi);
+        const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+        __nv_bfloat16 *row = jb + (r0 + rr) * (long long)(3 * kp) + c0 + cc;
+        row[0] = hi;
+        row[kp] = mid;
+        row[2 * kp] = lo;
+    }
+}
+
+// D*C = C_hi + C_lo in BF16 for the tensor cores: cm[n * kp + k] = hi,
+// cm[(kp + n) * kp + k] = lo, zero outside nc x nc.
+template <int NG>
+__global__ void k_build_cmat_bf16(const long long *__restrict__ row, const signed char *__restrict__ perm,
+                                  int nc, int kp, __nv_bfloat16 *__restrict__ cm) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)kp * kp) return;
+    const int n = (int)(idx / kp), k = (int)(idx % kp);
+    float c = 0.0f;
+    if (n < nc && k < nc) {
+        int pos[NG];
+        for (int a = 0; a < NG; a++) pos[perm[n * NG + a]] = a;
+        long long rank = 0;
+        unsigned used = 0;
+        for (int i = 0; i < NG; i++) {
+            const int ri = pos[perm[k * NG + i]];
+            rank = rank * (NG - i) + __popc(~used & ((1u << ri) - 1u));
+            used |= 1u << ri;
+        }
+        c = (float)row[rank];   // at most 15 significant bits: exact in FP32
+    }
+    const __nv_bfloat16 hi = __float2bfloat16_rn(c);
+    cm[idx] = hi;
+    cm[(long long)kp * kp + idx] = __float2bfloat16_rn(c - __bfloat162float(hi));
+}
+
 }  // namespace
 
 int mg_big_ngluon() { return BIG_NG; }
@@ -433,6 +491,24 @@ cudaError_t mg_launch_build_cbig(const long long *row, const signed char *perm, 
     const long long n = (long long)np * np;
     mg_note_launch();
     k_build_cbig<BIG_NG><<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(row, perm, nc, np, cbT);
+    return cudaGetLastError();
+}
+
+cudaError_t mg_launch_build_cmat_bf16(const long long *row, const signed char *perm, int nc, int kp,
+                                     __nv_bfloat16 *cm, cudaStream_t stream) {
+    if (kp < nc) return cudaErrorInvalidValue;
+    const long long n = (long long)kp * kp;
+    mg_note_launch();
+    k_build_cmat_bf16<BIG_NG><<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(row, perm, nc, kp, cm);
+    return cudaGetLastError();
+}
+
+cudaError_t mg_launch_rows_to_bf16(const double *jrow, long long R, int nsrc, int kp,
+                                   __nv_bfloat16 *jb, cudaStream_t stream) {
+    if (R <= 0) return cudaSuccess;
+    if (R % 64 || kp % 64) return cudaErrorInvalidValue;
+    mg_note_launch();
+    k_rows_to_bf16<<<dim3((unsigned)(R / 64), (unsigned)(kp / 64)), 256, 0, stream>>>(jrow, R, nsrc, kp, jb);
     return cudaGetLastError();
 }
 

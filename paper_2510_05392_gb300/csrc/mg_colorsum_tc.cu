@@ -418,6 +418,218 @@ __global__ void k_event_sum(const double *__restrict__ part, long long nevt, int
     me[e] = s * factor;
 }
 
+// ---------------------------------------------------------------------------
+// Colour sum of the 5040-flow process on the tensor cores.  The quadratic
+// form of every GEMM row V (3 BF16 pieces, KP colours) is taken over the
+// block upper triangle of D*C in 128 x 128 blocks:
+//   q_r = sum_I sum_{J >= I} w_IJ sum_{n in I} V_rn Z^(J)_rn,
+//   Z^(J)_rn = sum_{k in J} C_hat_nk V_rk,  w_II = 1, w_IJ = 2 (J > I).
+// Work item (M-tile of 128 rows, N-tile I), static round-robin over the
+// CTAs.  Each K-block J (two 64-colour chunks: 3 A pieces + C_hi, C_lo halves,
+// 80 KiB per chunk through a 2-stage ring) is accumulated in a fresh TMEM
+// accumulator (two alternate), so FP32 accumulation spans 128 colours as in
+// the single-tile kernel; the epilogue adds the blocks' dot products in FP64.
+// Roles: warp 0 TMA producer, warp 1 MMA issuer (one thread), warps 2-9
+// epilogue (lane quarter warp % 4, colour half (warp - 2) / 4 of the
+// N-tile; its 64 values of V held in registers for the whole item, read
+// once from the row buffer).  Writes part[(2 I + half) * R + r].
+constexpr int TB_STAGES = 2;
+constexpr int TB_CHUNK = 5 * TC_M * 128;          // bytes per K-chunk stage
+constexpr int TB_THREADS = 64 + 32 * 8;
+
+__global__ void __launch_bounds__(TB_THREADS, 1)
+    k_colorsum_tc_big(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                      const __nv_bfloat16 *__restrict__ jb, int kp, int np, long long mtiles,
+                      uint32_t extra_tx, double *__restrict__ part, long long R,
+                      int *__restrict__ err) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + TB_STAGES * TB_CHUNK);
+    uint64_t *empty = full + TB_STAGES;
+    uint64_t *tfull = empty + TB_STAGES;
+    uint64_t *tempty = tfull + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
+    int *failed = reinterpret_cast<int *>(tmem_slot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ntile_n = np / TC_M;                 // N-tiles = K-blocks
+    const long long nitems = mtiles * ntile_n;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(256)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 32) {
+        for (int i = 0; i < TB_STAGES; i++) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; i++) {
+            mbar_init(&tfull[i], 1);
+            mbar_init(&tempty[i], 8);
+        }
+        *failed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    // items in order: N-tile-major (the long items of small I first), M-tile minor
+    if (warp == 0) {
+        if (lane == 0) {  // ------------------------------------ producer
+            long long cc = 0;   // chunk counter over the CTA's items
+            bool ok = true;
+            for (long long it = blockIdx.x; ok && it < nitems; it += gridDim.x) {
+                const int I = (int)(it / mtiles);
+                const long long t = it % mtiles;
+                for (int kc = 2 * I; kc < 2 * ntile_n; kc++, cc++) {
+                    const int st = (int)(cc % TB_STAGES);
+                    const uint32_t ph = (uint32_t)((cc / TB_STAGES) & 1);
+                    if (*(volatile int *)failed || !mbar_wait(&empty[st], ph ^ 1, TC_WAIT_CYCLES)) {
+                        tc_fail(failed, err);
+                        ok = false;
+                        break;
+                    }
+                    unsigned char *dst = smem + st * TB_CHUNK;
+                    mbar_expect_tx(&full[st], (uint32_t)TB_CHUNK + extra_tx);
+                    for (int sp = 0; sp < 3; sp++)
+                        tma_load_2d(dst + sp * TC_M * 128, &tmA, sp * kp + kc * TC_KCHUNK,
+                                    (int)(t * TC_M), &full[st]);
+                    for (int h = 0; h < 2; h++)
+                        tma_load_2d(dst + (3 + h) * TC_M * 128, &tmB, kc * TC_KCHUNK,
+                                    h * np + I * TC_M, &full[st]);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {  // ------------------------------------ MMA issuer
+            const uint32_t idesc = instr_desc(TC_M, TC_M);
+            long long cc = 0, kb = 0;   // chunk and K-block counters
+            bool ok = true;
+            for (long long it = blockIdx.x; ok && it < nitems; it += gridDim.x) {
+                const int I = (int)(it / mtiles);
+                for (int J = I; ok && J < ntile_n; J++, kb++) {
+                    const int acc = (int)(kb & 1);
+                    const uint32_t aph = (uint32_t)((kb >> 1) & 1);
+                    if (*(volatile int *)failed || !mbar_wait(&tempty[acc], aph ^ 1, TC_WAIT_CYCLES)) {
+                        tc_fail(failed, err);
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t d = tmem + (uint32_t)(acc * TC_M);
+                    uint32_t accumulate = 0;
+                    for (int h = 0; h < 2; h++, cc++) {   // the block's two K-chunks
+                        const int st = (int)(cc % TB_STAGES);
+                        const uint32_t ph = (uint32_t)((cc / TB_STAGES) & 1);
+                        if (!mbar_wait(&full[st], ph, TC_WAIT_CYCLES)) {
+                            tc_fail(failed, err);
+                            ok = false;
+                            break;
+                        }
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const uint32_t base = smem_u32(smem + st * TB_CHUNK);
+                        const uint32_t bh = base + 3 * TC_M * 128, bl = base + 4 * TC_M * 128;
+                        for (int sp = 0; sp < 3; sp++) {
+                            const uint32_t a0 = base + sp * TC_M * 128;
+                            for (int k = 0; k < TC_KCHUNK / 16; k++) {
+                                mma_bf16(d, smem_desc(a0 + 32 * k), smem_desc(bh + 32 * k), idesc, accumulate);
+                                accumulate = 1;
+                            }
+                            if (sp < 2)
+                                for (int k = 0; k < TC_KCHUNK / 16; k++)
+                                    mma_bf16(d, smem_desc(a0 + 32 * k), smem_desc(bl + 32 * k), idesc, 1);
+                        }
+                        mma_commit(&empty[st]);
+                    }
+                    if (!ok) break;
+                    mma_commit(&tfull[acc]);
+                }
+            }
+        }
+    } else {  // ------------------------------------------------ epilogue
+        const int quarter = warp & 3;
+        const int half = (warp - 2) >> 2;
+        const int m = quarter * 32 + lane;
+        long long kb = 0;
+        bool ok = true;
+        for (long long it = blockIdx.x; ok && it < nitems; it += gridDim.x) {
+            const int I = (int)(it / mtiles);
+            const long long t = it % mtiles;
+            const long long r = t * TC_M + m;
+            // V of this row on the 64 colours of the N-tile half, hi + mid + lo
+            float v[64];
+            const __nv_bfloat16 *row = jb + r * (long long)(3 * kp) + I * TC_M + half * 64;
+#pragma unroll
+            for (int c8 = 0; c8 < 8; c8++) {
+                uint4 q[3];
+#pragma unroll
+                for (int sp = 0; sp < 3; sp++) q[sp] = *reinterpret_cast<const uint4 *>(row + sp * kp + 8 * c8);
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    float lo = 0.0f, hi = 0.0f;
+#pragma unroll
+                    for (int sp = 0; sp < 3; sp++) {
+                        const uint32_t w = (&q[sp].x)[i];
+                        lo += __uint_as_float(w << 16);
+                        hi += __uint_as_float(w & 0xFFFF0000u);
+                    }
+                    v[8 * c8 + 2 * i] = lo;
+                    v[8 * c8 + 2 * i + 1] = hi;
+                }
+            }
+            double total = 0.0;
+            for (int J = I; J < ntile_n; J++, kb++) {
+                const int acc = (int)(kb & 1);
+                const uint32_t aph = (uint32_t)((kb >> 1) & 1);
+                ok = __all_sync(0xffffffffu, !*(volatile int *)failed &&
+                                                 mbar_wait(&tfull[acc], aph, TC_WAIT_CYCLES));
+                if (!ok) {
+                    if (lane == 0) tc_fail(failed, err);
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t taddr = tmem + (uint32_t)(acc * TC_M + half * 64) + ((uint32_t)(quarter * 32) << 16);
+                float sh = 0.0f, sl = 0.0f;
+#pragma unroll
+                for (int g = 0; g < 4; g++) {
+                    uint32_t z[16];
+                    tmem_ld16(taddr + (uint32_t)(16 * g), z);
+#pragma unroll
+                    for (int j = 0; j < 16; j++) {
+                        const float vv = v[16 * g + j];
+                        const float zz = __uint_as_float(z[j]);
+                        const float p = vv * zz;
+                        const float pe = fmaf(vv, zz, -p);
+                        const float s = sh + p;
+                        const float bp = s - sh;
+                        const float se = (sh - (s - bp)) + (p - bp);
+                        sh = s;
+                        sl += se + pe;
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0)
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[acc]))
+                                 : "memory");
+                total += (J == I ? 1.0 : 2.0) * ((double)sh + (double)sl);
+            }
+            if (!ok) break;
+            part[(long long)(2 * I + half) * R + r] = total;
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        __syncwarp();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256)
+                     : "memory");
+    }
+}
+
 typedef CUresult (*encode_tiled_fn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
                                     const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
                                     const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -498,6 +710,32 @@ cudaError_t mg_launch_colorsum_tc(const __nv_bfloat16 *jbuf, long long ncols_all
     else
         k_colorsum_tc<2><<<(unsigned)grid, TC_THREADS, smem, stream>>>(ma, mb, np, np_pad, cpe, ntiles,
                                                                        tmem_cols, extra_tx, part, err);
+    return cudaGetLastError();
+}
+
+size_t mg_tc_big_smem_bytes() { return 1024 + (size_t)TB_STAGES * TB_CHUNK + (4 * TB_STAGES + 4) * 8 + 16; }
+
+cudaError_t mg_launch_colorsum_tc_big(const __nv_bfloat16 *jb, long long R, int kp,
+                                      const __nv_bfloat16 *cmat, int np, uint32_t extra_tx,
+                                      double *part, int *err, cudaStream_t stream) {
+    if (R <= 0) return cudaSuccess;
+    if (R % TC_M || kp % TC_M || np != kp) return cudaErrorInvalidValue;
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, jb, (uint64_t)R, (uint64_t)3 * kp, TC_M)) return cudaErrorInvalidValue;
+    if (!make_map(&mb, cmat, (uint64_t)2 * np, (uint64_t)kp, TC_M)) return cudaErrorInvalidValue;
+    const size_t smem = mg_tc_big_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(k_colorsum_tc_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, nsm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const long long mtiles = R / TC_M;
+    const long long nitems = mtiles * (np / TC_M);
+    const long long grid = nitems < nsm ? nitems : nsm;
+    mg_note_launch();
+    k_colorsum_tc_big<<<(unsigned)grid, TB_THREADS, smem, stream>>>(ma, mb, jb, kp, np, mtiles, extra_tx,
+                                                                     part, R, err);
     return cudaGetLastError();
 }
 

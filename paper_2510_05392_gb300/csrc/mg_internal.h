@@ -129,6 +129,10 @@ cudaError_t mg_launch_sigmakin_big(const mg_dev_proc &dp, const double *mom, lon
                                    const int *units, int nunits, int nsg, int nsf, double2 *scratch,
                                    long long T, double *jrow, long long R, long long nipad,
                                    cudaStream_t stream);
+cudaError_t mg_launch_build_cmat_bf16(const long long *row, const signed char *perm, int nc, int kp,
+                                     __nv_bfloat16 *cm, cudaStream_t stream);
+cudaError_t mg_launch_rows_to_bf16(const double *jrow, long long R, int nsrc, int kp,
+                                   __nv_bfloat16 *jb, cudaStream_t stream);
 cudaError_t mg_launch_colour_big(const double *jrow, long long R, const double *cbT, int np,
                                  double *qpart, cudaStream_t stream);
 cudaError_t mg_launch_event_sum_big(const double *qpart, long long R, int ntile, long long nipad,
@@ -138,6 +142,12 @@ cudaError_t mg_launch_event_sum_big(const double *qpart, long long R, int ntile,
 // graphs are not launches of this kind and are not counted)
 void mg_note_launch();
 int mg_tc_parts_per_tile(int cpe);
+// tensor-core colour sum of the table-file process over the block upper
+// triangle: jb [R][3*kp] BF16 rows, cmat [2*np][kp] (np == kp, multiples of
+// 128); writes part[(2 I + half) * R + r] for the 2 np / 128 colour halves
+cudaError_t mg_launch_colorsum_tc_big(const __nv_bfloat16 *jb, long long R, int kp,
+                                      const __nv_bfloat16 *cmat, int np, uint32_t extra_tx,
+                                      double *part, int *err, cudaStream_t stream);
 int mg_tc_parts_per_event(int cpe);
 // persistent multi-process kernel: counter reset + one launch of grid CTAs
 cudaError_t mg_launch_batch(const mg_batch_item *d_items, int nitems, unsigned long long *d_counter,

@@ -82,9 +82,30 @@ def test_colour_matrix_matches_oracle(big):
     assert np.array_equal(got, ref)
 
 
+MIXED_RTOL = 2e-6
+
+
+def test_mixed_colour_sum_on_tensor_cores(events):
+    """Colour sum of the 5040 flows on the tensor cores (BF16 pieces, FP32
+    accumulation per 128-colour block, blocks added in FP64) against the
+    oracle; per-helicity values against the FP64 path."""
+    mom, (ref, ref_h) = events
+    p = binding.Process(PROC, hel_mode=binding.MG_HEL_ALL, precision=binding.MG_MIXED_BF16)
+    md = torch.from_numpy(mom).cuda()
+    out = torch.empty(len(mom), dtype=torch.float64, device="cuda")
+    out_h = torch.empty((len(mom), 512), dtype=torch.float64, device="cuda")
+    p.sigmakin_hel(md, out, out_h)
+    torch.cuda.synchronize()
+    assert p.device_status() == 0
+    rel = np.abs(out.cpu().numpy() / ref - 1)
+    print(f"2->7 mixed: max rel {rel.max():.3e}")
+    assert rel.max() <= MIXED_RTOL
+    got_h = out_h.cpu().numpy()
+    scale = ref_h.max(axis=1, keepdims=True)            # per event
+    assert (np.abs(got_h - ref_h) <= MIXED_RTOL * scale).all()
+
+
 def test_unsupported_paths(big):
-    with pytest.raises(binding.MGError):
-        binding.Process(PROC, precision=binding.MG_MIXED_BF16)
     mom = torch.from_numpy(_events(1, 5)).cuda()
     with pytest.raises(binding.MGError):
         big.sigmakin_ex(mom, torch.empty(1, dtype=torch.float64, device="cuda"))

@@ -41,11 +41,12 @@ WORKLOADS = {
     "ggttgg_524288": ("g g > t t~ g g", 2, 524288, 1500.0, True, 20251005 + 2),
     "ggtt_16384": ("g g > t t~", 0, 16384, 1000.0, False, 20251005 + 1),
     "ggttggg_262144": ("g g > t t~ g g g", 3, 262144, 1500.0, True, 20251005 + 3),
+    "ggttgggg_16384": ("g g > t t~ g g g g", 4, 16384, 2000.0, True, 20251005 + 5),
     # 2 -> 7 (5040 flows): state in HBM, FP64 colour sum kernel of its own
     "ggttggggg_512": ("g g > t t~ g g g g g", 5, 512, 2000.0, True, 20251005 + 6),
 }
 # oracle events per CPU sample where one event takes seconds on the host
-CPU_SAMPLE_CAP = {"ggttggggg_512": 4}
+CPU_SAMPLE_CAP = {"ggttggggg_512": 4, "ggttgggg_16384": 256}
 TEST_SEED = 12345  # helicity-filter test events
 
 
@@ -517,8 +518,8 @@ def run_ours(args):
             bf16 = _measured_peak("bf16_tflops")
             roof_tc = {"bound": "tensor", "achieved": tc_ach, "peak": bf16, "unit": "TFLOP/s",
                        "frac": tc_ach / bf16 if bf16 else None, "traffic": None,
-                       "kernel": "k_colorsum_tc_big with its BF16 row conversion (peak = measured "
-                                 "cuBLAS bf16 burst)",
+                       "kernel": "k_colorsum_tc_big (2 -> 7: with its BF16 row conversion; peak = "
+                                 "measured cuBLAS bf16 burst)",
                        "launches_per_step": tc_n // args.steps,
                        "ms_per_step": tc_ms / args.steps, "flops_per_step": mma_flops}
         else:

@@ -65,7 +65,8 @@ typedef struct {
     int precision;   /* MG_FP64 (all FP64) or MG_MIXED_BF16 (FP64 diagrams, */
                      /* colour sum on tcgen05 tensor cores: jamps split in  */
                      /* three BF16 pieces, D*C in two, FP32 accumulation,   */
-                     /* FP64 epilogue; processes with <= 128 colour flows;  */
+                     /* FP64 epilogue; above 128 flows over the block upper */
+                     /* triangle in 128-colour blocks with FP64 block sums; */
                      /* mg_sigmakin_hel is then MG_ERR_UNSUPPORTED)        */
 } mg_params;
 

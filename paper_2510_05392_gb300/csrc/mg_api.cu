@@ -143,9 +143,13 @@ int set_hel_list(mg_process *p, const uint8_t *mask) {
 int setup_mixed(mg_process *p) {
     const mg_proc_table *t = p->tab;
     const int nc = t->ncolor;
-    if (nc > 128) return MG_ERR_UNSUPPORTED;  // tiles hold up to 128 colour flows
-    p->kp = 64 * ((nc + 63) / 64);
-    p->np = 16 * ((nc + 15) / 16);
+    if (nc <= 128) {   // one tile holds every colour flow
+        p->kp = 64 * ((nc + 63) / 64);
+        p->np = 16 * ((nc + 15) / 16);
+    } else {           // block upper triangle in 128-colour blocks
+        p->kp = 128 * ((nc + 127) / 128);
+        p->np = p->kp;
+    }
     const size_t n = (size_t)2 * p->np * p->kp;
     __nv_bfloat16 *h = (__nv_bfloat16 *)calloc(n, sizeof(__nv_bfloat16));
     if (!h) return MG_ERR_NO_MEMORY;
@@ -739,8 +743,11 @@ static int sigmakin_mixed(mg_process *p, const double *mom, int64_t nevt, double
     if (chunk < ev_align) chunk = ev_align;
     if (chunk > nevt) chunk = (nevt + ev_align - 1) / ev_align * ev_align;
     const long long rows = (chunk * cpe + 127) / 128 * 128;
-    const int per_event = mg_tc_parts_per_event(cpe);
-    const long long parts = rows / 128 * mg_tc_parts_per_tile(cpe);
+    // more than 128 flows: the block-triangular kernel, one partial per row
+    // and half of a 128-colour block
+    const bool big_tc = p->tab->ncolor > 128;
+    const int per_event = big_tc ? 0 : mg_tc_parts_per_event(cpe);
+    const long long parts = big_tc ? rows * (2 * p->np / 128) : rows / 128 * mg_tc_parts_per_tile(cpe);
     if (rows > p->jbuf_rows) {
         cudaFree(p->d_jbuf);
         p->d_jbuf = nullptr;
@@ -771,11 +778,19 @@ static int sigmakin_mixed(mg_process *p, const double *mom, int64_t nevt, double
                                    p->block, nullptr, nullptr, s, p->d_jbuf, p->kp, nup));
         mg_timer_end(p, s, slot);
         slot = mg_timer_begin(p, s, MG_KT_COLOUR);
-        MG_CUDA(mg_launch_colorsum_tc(p->d_jbuf, used, p->kp, p->d_cmat, p->np, p->tab->ncolor,
-                                      cpe, p->debug_extra_tx, p->d_part, p->d_err, s));
+        if (big_tc)
+            MG_CUDA(mg_launch_colorsum_tc_big(p->d_jbuf, used, p->kp, p->d_cmat, p->np,
+                                              p->debug_extra_tx, p->d_part, p->d_err, s));
+        else
+            MG_CUDA(mg_launch_colorsum_tc(p->d_jbuf, used, p->kp, p->d_cmat, p->np, p->tab->ncolor,
+                                          cpe, p->debug_extra_tx, p->d_part, p->d_err, s));
         mg_timer_end(p, s, slot);
         slot = mg_timer_begin(p, s, MG_KT_EVENT_SUM);
-        MG_CUDA(mg_launch_event_sum(p->d_part, n, per_event, p->factor, me + e0, s));
+        if (big_tc)
+            MG_CUDA(mg_launch_event_sum_rows(p->d_part, used, 2 * p->np / 128, cpe, n, p->factor,
+                                             me + e0, s));
+        else
+            MG_CUDA(mg_launch_event_sum(p->d_part, n, per_event, p->factor, me + e0, s));
         mg_timer_end(p, s, slot);
     }
     return MG_OK;

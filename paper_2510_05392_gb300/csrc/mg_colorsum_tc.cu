@@ -630,6 +630,18 @@ __global__ void __launch_bounds__(TB_THREADS, 1)
     }
 }
 
+// me[e] = factor * sum over the event's cpe rows (contiguous from e * cpe)
+// and the ncols partial columns part[c * R + r], in that fixed order.
+__global__ void k_event_sum_rows(const double *__restrict__ part, long long R, int ncols, int cpe,
+                                 long long nevt, double factor, double *__restrict__ me) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nevt) return;
+    double s = 0.0;
+    for (int j = 0; j < cpe; j++)
+        for (int c = 0; c < ncols; c++) s += part[(long long)c * R + e * cpe + j];
+    me[e] = s * factor;
+}
+
 typedef CUresult (*encode_tiled_fn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
                                     const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
                                     const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -736,6 +748,15 @@ cudaError_t mg_launch_colorsum_tc_big(const __nv_bfloat16 *jb, long long R, int 
     mg_note_launch();
     k_colorsum_tc_big<<<(unsigned)grid, TB_THREADS, smem, stream>>>(ma, mb, jb, kp, np, mtiles, extra_tx,
                                                                      part, R, err);
+    return cudaGetLastError();
+}
+
+cudaError_t mg_launch_event_sum_rows(const double *part, long long R, int ncols, int cpe, long long nevt,
+                                     double factor, double *me, cudaStream_t stream) {
+    if (nevt <= 0) return cudaSuccess;
+    if (nevt * cpe > R) return cudaErrorInvalidValue;
+    mg_note_launch();
+    k_event_sum_rows<<<(unsigned)((nevt + 127) / 128), 128, 0, stream>>>(part, R, ncols, cpe, nevt, factor, me);
     return cudaGetLastError();
 }
 

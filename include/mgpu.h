@@ -192,7 +192,8 @@ int mg_sigmakin_ex(mg_process *p, const double *momenta_dev, int64_t nevt,
                    const mg_sigmakin_extras *extras, double *me_out_dev, void *stream);
 
 /* Launch shape: threads per event (1..32, power of two) and threads per
- * block (multiple of 32, <= 1024).  0 keeps the current value. */
+ * block (multiple of 32, <= 128: the diagram kernel keeps three 128-thread
+ * blocks resident per SM).  0 keeps the current value. */
 int mg_set_launch(mg_process *p, int threads_per_event, int block);
 
 int mg_process_info(const mg_process *p, mg_info *out);

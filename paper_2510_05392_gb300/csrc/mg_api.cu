@@ -661,8 +661,8 @@ int mg_set_launch(mg_process *p, int tpe, int block) {
         if (tpe < 1 || tpe > 32 || (tpe & (tpe - 1))) return MG_ERR_BAD_ARG;
         p->tpe = tpe;
     }
-    if (block) {
-        if (block < 32 || block > 1024 || block % 32) return MG_ERR_BAD_ARG;
+    if (block) {   // the diagram kernel is compiled for blocks of at most 128 threads
+        if (block < 32 || block > 128 || block % 32) return MG_ERR_BAD_ARG;
         p->block = block;
     }
     return MG_OK;

@@ -209,8 +209,11 @@ __device__ void write_jamp_rows(const cx (*J)[4], int mask, __nv_bfloat16 *__res
     }
 }
 
+// Plain instantiations: three 128-thread blocks per SM (167 registers, no
+// spills; the FP64 pipe then has 12 warps to hide local-memory latency with);
+// the extras instantiation keeps the register budget of 256-thread blocks.
 template <int NG, int NSG, int NSF, int NSA, int NC, bool EX>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(EX ? 256 : 128, EX ? 1 : 3)
     k_sigmakin(const double *__restrict__ mom, long long nevt, const int4 *__restrict__ ops,
                int nops, const int *__restrict__ scat, const double *__restrict__ cup,
                const int *__restrict__ units, int nunits, int tpe, double mt, double wt,

@@ -106,7 +106,7 @@ def test_launch_shapes_agree(tpe):
     p = _filtered(proc, 2, sqrts)
     ref = torch.empty(301, dtype=torch.float64, device="cuda")
     p.sigmakin(mom, ref)
-    p.set_launch(threads_per_event=tpe, block=64 if tpe < 8 else 256)
+    p.set_launch(threads_per_event=tpe, block=64 if tpe < 8 else 128)
     out = torch.empty_like(ref)
     p.sigmakin(mom, out)
     torch.cuda.synchronize()

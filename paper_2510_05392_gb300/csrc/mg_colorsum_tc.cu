@@ -158,6 +158,15 @@ constexpr int TC_NGROUP = 2;                  // epilogue groups, one per TMEM a
 constexpr int TC_GROUP_WARPS = 4 * TC_NSPLIT;
 constexpr int TC_EPI_WARPS = TC_NGROUP * TC_GROUP_WARPS;
 constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;
+// Each epilogue group has a ring of its own (stages [TC_RING g, TC_RING (g + 1))):
+// a stage is then filled and released by one group only, in order, so a
+// parity wait can never mistake another group's earlier fill for its own.
+constexpr int TC_RING = TC_STAGES / TC_NGROUP;
+
+__device__ __forceinline__ void ring_slot(int grp, long long q, int &stage, uint32_t &phase) {
+    stage = grp * TC_RING + (int)(q % TC_RING);
+    phase = (uint32_t)((q / TC_RING) & 1);
+}
 
 struct TcSmem {
     uint64_t *bB, *full, *empty, *tfull, *tempty;
@@ -228,10 +237,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (int h = 0; h < 2; h++)
                 for (int kc = 0; kc < kc_n; kc++)
                     tma_load_2d(sB + (h * kc_n + kc) * b_chunk, &tmB, kc * TC_KCHUNK, h * np, S.bB);
-            int stage = 0;
-            uint32_t phase = 0;
-            for (long long t = blockIdx.x; t < ntiles && !*(volatile int *)S.failed; t += gridDim.x) {
+            long long q[TC_NGROUP] = {0, 0};   // fills per ring
+            int k = 0;                          // tile index among this CTA's tiles
+            for (long long t = blockIdx.x; t < ntiles && !*(volatile int *)S.failed; t += gridDim.x, k++) {
+                const int g = k % TC_NGROUP;
                 for (int c = 0; c < nchunk; c++) {
+                    int stage;
+                    uint32_t phase;
+                    ring_slot(g, q[g]++, stage, phase);
                     if (!mbar_wait(&S.empty[stage], phase ^ 1, TC_WAIT_CYCLES)) {
                         tc_fail(S.failed, err);
                         break;
@@ -240,10 +253,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     const int sp = c / kc_n, kc = c % kc_n;
                     tma_load_2d(sA + stage * a_chunk, &tmA, sp * kp + kc * TC_KCHUNK, (int)(t * TC_M),
                                 &S.full[stage]);
-                    if (++stage == TC_STAGES) {
-                        stage = 0;
-                        phase ^= 1;
-                    }
                 }
             }
         }
@@ -252,9 +261,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             bool ok = mbar_wait(S.bB, 0, TC_WAIT_CYCLES);
             if (!ok) tc_fail(S.failed, err);
             const uint32_t idesc = instr_desc(TC_M, np);
-            int stage = 0;
-            uint32_t phase = 0, aphase = 0;
-            int acc = 0;
+            long long q[TC_NGROUP] = {0, 0};   // fills per ring
+            uint32_t aphase = 0;
+            int acc = 0;                        // = tile index % 2 = the tile's group
             for (long long t = blockIdx.x; ok && t < ntiles && !*(volatile int *)S.failed; t += gridDim.x) {
                 if (!mbar_wait(&S.tempty[acc], aphase ^ 1, TC_WAIT_CYCLES)) {
                     tc_fail(S.failed, err);
@@ -264,6 +273,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const uint32_t d = tmem + (uint32_t)(acc * np_pad);
                 uint32_t accumulate = 0;
                 for (int c = 0; c < nchunk; c++) {
+                    int stage;
+                    uint32_t phase;
+                    ring_slot(acc, q[acc]++, stage, phase);
                     if (!mbar_wait(&S.full[stage], phase, TC_WAIT_CYCLES)) {
                         tc_fail(S.failed, err);
                         ok = false;
@@ -282,10 +294,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         for (int k = 0; k < TC_KCHUNK / 16; k++)
                             mma_bf16(d, smem_desc(a0 + 32 * k), smem_desc(bl + 32 * k), idesc, 1);
                     mma_commit(&S.empty[stage]);
-                    if (++stage == TC_STAGES) {
-                        stage = 0;
-                        phase ^= 1;
-                    }
                 }
                 if (!ok) break;
                 mma_commit(&S.tfull[acc]);
@@ -315,9 +323,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             float v[kp / TC_NSPLIT];            // v[16 (g / TC_NSPLIT) + j] = V of colour 16 g + j
 #pragma unroll
             for (int c = 0; c < nchunk; c++) {
-                const long long gch = i * nchunk + c;   // chunk's place in the CTA's sequence
-                const int stage = (int)(gch % TC_STAGES);
-                const uint32_t phase = (uint32_t)((gch / TC_STAGES) & 1);
+                int stage;
+                uint32_t phase;
+                ring_slot(grp, (i / TC_NGROUP) * nchunk + c, stage, phase);   // this group's ring
                 if (ok)
                     ok = __all_sync(0xffffffffu, !*(volatile int *)S.failed &&
                                                      mbar_wait(&S.full[stage], phase, TC_WAIT_CYCLES));
@@ -347,6 +355,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             }
                         }
                     }
+                    // the stage goes back to the TMA producer: this thread's
+                    // shared-memory reads (generic proxy) must be complete
+                    // before the next copy (async proxy) may overwrite it
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     __syncwarp();
                     if (lane == 0)
                         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(

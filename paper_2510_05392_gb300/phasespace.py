@@ -198,6 +198,8 @@ WORKLOADS = {
     "ggtt_16384": dict(ngluon_final=0, nevt=16384, sqrts=1000.0, cuts=False, seed=20251005 + 1),
     "ggttgg_524288": dict(ngluon_final=2, nevt=524288, sqrts=1500.0, cuts=True, seed=20251005 + 2),
     "ggttggg_262144": dict(ngluon_final=3, nevt=262144, sqrts=1500.0, cuts=True, seed=20251005 + 3),
+    "ggttgggg_16384": dict(ngluon_final=4, nevt=16384, sqrts=2000.0, cuts=True, seed=20251005 + 5),
+    "ggttggggg_512": dict(ngluon_final=5, nevt=512, sqrts=2000.0, cuts=True, seed=20251005 + 6),
 }
 
 

@@ -107,9 +107,9 @@ int mg_process_create(const char *process, const mg_params *params, mg_process *
  * runs on the tensor cores instead (jamps as three BF16 pieces, D*C as
  * C_hi + C_lo, FP32 accumulation per 128-colour block, blocks added in FP64;
  * relative error about 1e-6).  mg_sigmakin, mg_sigmakin_hel, mg_filter_helicities,
- * mg_color_matrix and the timing hooks work as for the other processes;
- * mg_sigmakin_ex, the batch calls and mg_filter_helicities_noalloc return
- * MG_ERR_UNSUPPORTED. */
+ * mg_color_matrix, mg_sigmakin_ex (in both precisions) and the timing hooks
+ * work as for the other processes; the batch calls and
+ * mg_filter_helicities_noalloc return MG_ERR_UNSUPPORTED. */
 int mg_process_create_from_tables(const char *table_path, const mg_params *params, mg_process **out);
 
 /* Helicity filter (Sec. 2.2 and Sec. 4.6 of the paper: keep the helicities with
@@ -156,8 +156,8 @@ int mg_sigmakin_hel(mg_process *p, const double *momenta_dev, int64_t nevt, doub
  * MG_OK. */
 int mg_device_status(mg_process *p, void *stream);
 
-/* Per-event extras of sigmaKin (FP64 path; all pointers device, optional
- * unless stated).  The paper's production kernel also takes an event-by-
+/* Per-event extras of sigmaKin (FP64 path, and both precisions of the
+ * table-file process; all pointers device, optional unless stated).  The paper's production kernel also takes an event-by-
  * event alpha_s, random numbers for a helicity and a colour choice, and a
  * channel id for single-diagram enhancement (Sec. 2.2):
  *   alphas_dev       [nevt] per-event alpha_s.  Every vertex is QCD, so
@@ -166,8 +166,9 @@ int mg_device_status(mg_process *p, void *stream);
  *   channel          colour-factor class used as the enhancement channel, or
  *                    -1.  The classes of diagram terms whose colour factors
  *                    agree up to a phase are as many as the paper's channels
- *                    (3 / 15 / 105 / 945); channel c's amplitude is the sum
- *                    of its class's terms.
+ *                    (3 / 15 / 105 / 945; 10395 and 135135 for 6 and 7
+ *                    gluons); channel c's amplitude is the sum of its class's
+ *                    terms.
  *   sde_weight_dev   out [nevt] (required when channel >= 0):
  *                    sum_h |A_c,h|^2 / sum_h sum_c' |A_c',h|^2 (good helicities)
  *   flow_weight_dev  out [nevt][ncolor]: sum over good helicities of |J_s|^2

@@ -179,8 +179,18 @@ int setup_mixed(mg_process *p) {
 // the rows are cleared, the diagram kernel accumulates the jamps into them,
 // the colour-sum kernel forms every row's quadratic form per 64-colour tile
 // and the event sum adds them up.
+// Per-event extras of a table-file process (mg_sigmakin_ex): alphas [nevt]
+// or NULL, channel and sde [nevt] (channel >= 0), flow weights jw
+// [nevt][ncolor] or NULL.
+struct BigExtras {
+    const double *alphas;
+    int channel;
+    double *sde;
+    double *jw;
+};
+
 int sigmakin_big(mg_process *p, const double *mom, int64_t nevt, double *me, double *me_hel,
-                 cudaStream_t s) {
+                 cudaStream_t s, const BigExtras *bx = nullptr) {
     const mg_proc_table *t = p->tab;
     const int nu = p->nunits;
     const int nhel = 1 << t->npar;
@@ -242,33 +252,57 @@ int sigmakin_big(mg_process *p, const double *mom, int64_t nevt, double *me, dou
         if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? MG_ERR_NO_MEMORY : cuda_fail(e);
         p->jrow_items = nipad_max;
     }
+    double *sde_item = nullptr;   // per-item channel sums, one chunk
+    const bool want_sde = bx && bx->channel >= 0;
+    if (want_sde) {
+        cudaError_t e = cudaMalloc(&sde_item, sizeof(double) * 8 * nipad_max);
+        if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? MG_ERR_NO_MEMORY : cuda_fail(e);
+    }
+    int rc = MG_OK;
     const mg_dev_proc dp = dev_view(p);
     for (long long e0 = 0; e0 < nevt; e0 += ev_chunk) {
         const long long n = (nevt - e0 < ev_chunk) ? nevt - e0 : ev_chunk;
         const long long nitem = n * nu;
         const long long nip = (nitem + ipad - 1) / ipad * ipad;
         const long long R = 8 * nip;
-        MG_CUDA(cudaMemsetAsync(p->d_jrow, 0, sizeof(double) * np * R, s));
+        cudaError_t e = cudaMemsetAsync(p->d_jrow, 0, sizeof(double) * np * R, s);
         int slot = mg_timer_begin(p, s, MG_KT_DIAGRAM);
-        MG_CUDA(mg_launch_sigmakin_big(dp, mom + e0 * t->npar * 4, nitem, p->d_units, nu, t->nslot,
-                                       t->nslot_top, p->d_scratch, T, p->d_jrow, R, nip, s));
+        if (e == cudaSuccess)
+            e = mg_launch_sigmakin_big(dp, mom + e0 * t->npar * 4, nitem, p->d_units, nu, t->nslot,
+                                       t->nslot_top, p->d_scratch, T, p->d_jrow, R, nip, s,
+                                       want_sde ? bx->channel : -1, sde_item);
         mg_timer_end(p, s, slot);
         slot = mg_timer_begin(p, s, MG_KT_COLOUR);
-        if (mixed) {
-            MG_CUDA(mg_launch_rows_to_bf16(p->d_jrow, R, (int)np, p->kp, p->d_jbuf, s));
-            MG_CUDA(mg_launch_colorsum_tc_big(p->d_jbuf, R, p->kp, p->d_cmat, p->np, p->debug_extra_tx,
-                                              p->d_qpart, p->d_err, s));
-        } else {
-            MG_CUDA(mg_launch_colour_big(p->d_jrow, R, p->d_cbig, (int)np, p->d_qpart, s));
+        if (e == cudaSuccess && mixed) {
+            e = mg_launch_rows_to_bf16(p->d_jrow, R, (int)np, p->kp, p->d_jbuf, s);
+            if (e == cudaSuccess)
+                e = mg_launch_colorsum_tc_big(p->d_jbuf, R, p->kp, p->d_cmat, p->np, p->debug_extra_tx,
+                                              p->d_qpart, p->d_err, s);
+        } else if (e == cudaSuccess) {
+            e = mg_launch_colour_big(p->d_jrow, R, p->d_cbig, (int)np, p->d_qpart, s);
         }
         mg_timer_end(p, s, slot);
         slot = mg_timer_begin(p, s, MG_KT_EVENT_SUM);
-        MG_CUDA(mg_launch_event_sum_big(p->d_qpart, R, ntile, nip, p->d_units, nu, n, p->factor,
-                                        me ? me + e0 : nullptr, me_hel ? me_hel + e0 * nhel : nullptr,
-                                        s));
+        if (e == cudaSuccess)
+            e = mg_launch_event_sum_big(p->d_qpart, R, ntile, nip, p->d_units, nu, n, p->factor,
+                                        me ? me + e0 : nullptr, me_hel ? me_hel + e0 * nhel : nullptr, s,
+                                        bx && bx->alphas ? bx->alphas + e0 : nullptr, p->par.alphas,
+                                        sde_item, want_sde ? bx->sde + e0 : nullptr);
         mg_timer_end(p, s, slot);
+        if (e == cudaSuccess && bx && bx->jw)
+            e = mg_launch_flow_weights_big(p->d_jrow, R, nip, p->d_units, nu, n, t->ncolor,
+                                           bx->jw + e0 * t->ncolor, s);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e);
+            break;
+        }
     }
-    return MG_OK;
+    if (sde_item) {   // the chunk kernels read it: release after they ran
+        cudaError_t e = cudaStreamSynchronize(s);
+        cudaFree(sde_item);
+        if (rc == MG_OK && e != cudaSuccess) rc = cuda_fail(e);
+    }
+    return rc;
 }
 
 // Checks every index a table-file program can use against its pools, so a
@@ -1019,7 +1053,7 @@ extern "C" int mg_sigmakin_ex(mg_process *p, const double *mom, int64_t nevt,
                               const mg_sigmakin_extras *x, double *me, void *stream) {
     if (!p || !x || nevt < 0) return MG_ERR_BAD_ARG;
     if (p->ngood < 0) return MG_ERR_NOT_FILTERED;
-    if (p->par.precision != MG_FP64 || p->big) return MG_ERR_UNSUPPORTED;
+    if (p->par.precision != MG_FP64 && !p->big) return MG_ERR_UNSUPPORTED;
     if (nevt == 0) return MG_OK;
     int st = check_dev_ptr(mom, p->device);
     if (!st && me) st = check_dev_ptr(me, p->device);
@@ -1048,6 +1082,17 @@ extern "C" int mg_sigmakin_ex(mg_process *p, const double *mom, int64_t nevt,
     double *mh = want_hel ? p->d_sel_hel : nullptr;
     double *jw = x->flow_weight_dev ? x->flow_weight_dev : (want_col ? p->d_sel_jw : nullptr);
     if (mh) MG_CUDA(cudaMemsetAsync(mh, 0, sizeof(double) * nevt * nhel, s));
+    if (p->big) {   // table-file process: extras from the chunked HBM pipeline
+        const BigExtras bx = {x->alphas_dev, x->channel, x->channel >= 0 ? x->sde_weight_dev : nullptr, jw};
+        if (!me && !mh && !jw && x->channel < 0) return MG_OK;
+        st = sigmakin_big(p, mom, nevt, me, mh, s, &bx);
+        if (st) return st;
+        if (want_hel || want_col)
+            MG_CUDA(mg_launch_select(mh, nhel, jw, nc, nevt, x->rnd_hel_dev, x->rnd_col_dev,
+                                     want_hel ? x->hel_out_dev : nullptr, want_col ? x->col_out_dev : nullptr,
+                                     s));
+        return MG_OK;
+    }
     mg_extras ex;
     ex.alphas = x->alphas_dev;
     ex.alphas0 = p->par.alphas;

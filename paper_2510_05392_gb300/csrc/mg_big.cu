@@ -114,11 +114,13 @@ __device__ __forceinline__ void prefetch_inputs(const int4 &a, const int4 &b, co
 // F (slot s, variant v, component m: 8 s + 4 v + m), A (slot s, variant v:
 // 4 s + v); jamp (c, v) real part at jr[c * R + 2 v * nipad], imaginary part
 // one row block further.
+// sde8 (may be NULL): per top-helicity combination v, |A_channel|^2 in [v]
+// and the sum over colour-factor classes of |A_class|^2 in [4 + v].
 template <int NG>
 __device__ void run_item(const Kin<NG> &k, int g, const int4 *__restrict__ ops, int nops,
                          const int *__restrict__ scat, double mt, const Strided &WG,
                          const Strided &WF, const Strided &ACC, double *__restrict__ jr, long long R,
-                         long long nipad) {
+                         long long nipad, int channel, double *sde8) {
     cx G0[4][4];
     int4 an = __ldg(ops), bn = __ldg(ops + 1);
     for (int i = 0; i < nops; i++) {
@@ -244,6 +246,13 @@ __device__ void run_item(const Kin<NG> &k, int g, const int4 *__restrict__ ops, 
                         break;
                     }
                 }
+                if (sde8) {  // channel weight: |A_class|^2 over all classes and the chosen one
+                    for (int v = 0; v < 4; v++) {
+                        const double w = fma(amp[v].r, amp[v].r, amp[v].i * amp[v].i);
+                        sde8[4 + v] += w;
+                        if (a.y == channel) sde8[v] += w;
+                    }
+                }
                 // jamp updates in batches: every old value of a batch is
                 // loaded before any is stored (the flows of one scatter list
                 // are distinct), so the batch waits for memory once
@@ -286,7 +295,7 @@ __global__ void __launch_bounds__(BIG_BLOCK, 3)   // 168 registers: three blocks
                    const int *__restrict__ units, const int4 *__restrict__ ops, int nops,
                    const int *__restrict__ scat, double mt, double wt, double2 *__restrict__ scratch,
                    long long T, int nsg, int nsf, double *__restrict__ jrow, long long R,
-                   long long nipad) {
+                   long long nipad, int channel, double *__restrict__ sde_item) {
     constexpr int NPAR = NG + 2;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T) return;
@@ -298,7 +307,11 @@ __global__ void __launch_bounds__(BIG_BLOCK, 3)   // 168 registers: three blocks
         const int u = __ldg(units + (item - e * nunits));
         Kin<NG> k;
         kinematics<NG>(k, mom + e * (NPAR * 4), mt, wt);
-        run_item<NG>(k, u >> 4, ops, nops, scat, mt, WG, WF, ACC, jrow + item, R, nipad);
+        double sde8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        run_item<NG>(k, u >> 4, ops, nops, scat, mt, WG, WF, ACC, jrow + item, R, nipad, channel,
+                     sde_item ? sde8 : nullptr);
+        if (sde_item)
+            for (int q = 0; q < 8; q++) sde_item[item * 8 + q] = sde8[q];
     }
 }
 
@@ -356,14 +369,24 @@ __global__ void __launch_bounds__(256)
 
 // Per event: sum over its items (units), good helicity combinations,
 // real/imaginary rows and colour tiles, in that fixed order.
+// Per-event extras: |M|^2 ~ alpha_s^NG, so alphas (may be NULL) rescales the
+// event by (alphas[e] / alphas0)^NG; sde (with sde_item) is the event's
+// channel weight over its good helicities.
 template <int NG>
 __global__ void k_event_sum_big(const double *__restrict__ qpart, long long R, int ntile,
                                 long long nipad, const int *__restrict__ units, int nunits,
                                 long long nevt, double factor, double *__restrict__ me,
-                                double *__restrict__ me_hel) {
+                                double *__restrict__ me_hel, const double *__restrict__ alphas,
+                                double alphas0, const double *__restrict__ sde_item,
+                                double *__restrict__ sde) {
     constexpr int NPAR = NG + 2;
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nevt) return;
+    if (alphas) {
+        const double r = alphas[e] / alphas0;
+        for (int i = 0; i < NG; i++) factor *= r;
+    }
+    double num = 0.0, den = 0.0;
     double tot = 0.0;
     for (int iu = 0; iu < nunits; iu++) {
         const long long item = e * nunits + iu;
@@ -377,9 +400,37 @@ __global__ void k_event_sum_big(const double *__restrict__ qpart, long long R, i
             }
             tot += mh;
             if (me_hel) me_hel[e * (1LL << NPAR) + helicity_index<NG>(u >> 4, v >> 1, v & 1)] = mh * factor;
+            if (sde_item) {
+                num += sde_item[item * 8 + v];
+                den += sde_item[item * 8 + 4 + v];
+            }
         }
     }
     if (me) me[e] = tot * factor;
+    if (sde) sde[e] = den > 0.0 ? num / den : 0.0;
+}
+
+// Helicity-summed |J_s|^2 per event and flow (jamps without couplings, good
+// helicities only) from the FP64 jamp rows: jw[e * ncolor + c].
+__global__ void k_flow_weights_big(const double *__restrict__ jrow, long long R, long long nipad,
+                                   const int *__restrict__ units, int nunits, long long nevt,
+                                   int ncolor, double *__restrict__ jw) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nevt * ncolor) return;
+    const long long e = idx / ncolor;
+    const int c = (int)(idx % ncolor);
+    const double *col = jrow + (long long)c * R;
+    double w = 0.0;
+    for (int iu = 0; iu < nunits; iu++) {
+        const long long item = e * nunits + iu;
+        const int u = __ldg(units + iu);
+        for (int v = 0; v < 4; v++) {
+            if (!((u >> v) & 1)) continue;
+            const double re = col[2 * v * nipad + item], im = col[(2 * v + 1) * nipad + item];
+            w = fma(re, re, fma(im, im, w));
+        }
+    }
+    jw[idx] = w;
 }
 
 // Block upper triangle of D*C, transposed for the k-major tiles:
@@ -515,13 +566,24 @@ cudaError_t mg_launch_rows_to_bf16(const double *jrow, long long R, int nsrc, in
 cudaError_t mg_launch_sigmakin_big(const mg_dev_proc &dp, const double *mom, long long nitem,
                                    const int *units, int nunits, int nsg, int nsf, double2 *scratch,
                                    long long T, double *jrow, long long R, long long nipad,
-                                   cudaStream_t stream) {
+                                   cudaStream_t stream, int channel, double *sde_item) {
     if (nitem <= 0) return cudaSuccess;
     if (T <= 0 || T % BIG_BLOCK || R != 8 * nipad || nipad < nitem) return cudaErrorInvalidValue;
     mg_note_launch();
     k_sigmakin_big<BIG_NG><<<(unsigned)(T / BIG_BLOCK), BIG_BLOCK, 0, stream>>>(
         mom, nitem, nunits, units, reinterpret_cast<const int4 *>(dp.ops), dp.nops, dp.scat, dp.mt,
-        dp.wt, scratch, T, nsg, nsf, jrow, R, nipad);
+        dp.wt, scratch, T, nsg, nsf, jrow, R, nipad, channel, sde_item);
+    return cudaGetLastError();
+}
+
+cudaError_t mg_launch_flow_weights_big(const double *jrow, long long R, long long nipad,
+                                       const int *units, int nunits, long long nevt, int ncolor,
+                                       double *jw, cudaStream_t stream) {
+    if (nevt <= 0) return cudaSuccess;
+    const long long n = nevt * ncolor;
+    mg_note_launch();
+    k_flow_weights_big<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(jrow, R, nipad, units, nunits,
+                                                                         nevt, ncolor, jw);
     return cudaGetLastError();
 }
 
@@ -537,10 +599,13 @@ cudaError_t mg_launch_colour_big(const double *jrow, long long R, const double *
 
 cudaError_t mg_launch_event_sum_big(const double *qpart, long long R, int ntile, long long nipad,
                                     const int *units, int nunits, long long nevt, double factor,
-                                    double *me, double *me_hel, cudaStream_t stream) {
+                                    double *me, double *me_hel, cudaStream_t stream,
+                                    const double *alphas, double alphas0, const double *sde_item,
+                                    double *sde) {
     if (nevt <= 0) return cudaSuccess;
     mg_note_launch();
     k_event_sum_big<BIG_NG><<<(unsigned)((nevt + 127) / 128), 128, 0, stream>>>(
-        qpart, R, ntile, nipad, units, nunits, nevt, factor, me, me_hel);
+        qpart, R, ntile, nipad, units, nunits, nevt, factor, me, me_hel, alphas, alphas0, sde_item,
+        sde);
     return cudaGetLastError();
 }

@@ -128,7 +128,10 @@ cudaError_t mg_launch_build_cbig(const long long *row, const signed char *perm, 
 cudaError_t mg_launch_sigmakin_big(const mg_dev_proc &dp, const double *mom, long long nitem,
                                    const int *units, int nunits, int nsg, int nsf, double2 *scratch,
                                    long long T, double *jrow, long long R, long long nipad,
-                                   cudaStream_t stream);
+                                   cudaStream_t stream, int channel = -1, double *sde_item = nullptr);
+cudaError_t mg_launch_flow_weights_big(const double *jrow, long long R, long long nipad,
+                                       const int *units, int nunits, long long nevt, int ncolor,
+                                       double *jw, cudaStream_t stream);
 cudaError_t mg_launch_build_cmat_bf16(const long long *row, const signed char *perm, int nc, int kp,
                                      __nv_bfloat16 *cm, cudaStream_t stream);
 cudaError_t mg_launch_rows_to_bf16(const double *jrow, long long R, int nsrc, int kp,
@@ -137,7 +140,9 @@ cudaError_t mg_launch_colour_big(const double *jrow, long long R, const double *
                                  double *qpart, cudaStream_t stream);
 cudaError_t mg_launch_event_sum_big(const double *qpart, long long R, int ntile, long long nipad,
                                     const int *units, int nunits, long long nevt, double factor,
-                                    double *me, double *me_hel, cudaStream_t stream);
+                                    double *me, double *me_hel, cudaStream_t stream,
+                                    const double *alphas = nullptr, double alphas0 = 0.0,
+                                    const double *sde_item = nullptr, double *sde = nullptr);
 // counts a kernel launch of the library (measurement; replays of captured
 // graphs are not launches of this kind and are not counted)
 void mg_note_launch();

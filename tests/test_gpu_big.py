@@ -107,5 +107,50 @@ def test_mixed_colour_sum_on_tensor_cores(events):
 
 def test_unsupported_paths(big):
     mom = torch.from_numpy(_events(1, 5)).cuda()
-    with pytest.raises(binding.MGError):
-        big.sigmakin_ex(mom, torch.empty(1, dtype=torch.float64, device="cuda"))
+    with pytest.raises(binding.MGError):       # the fixed-scratch filter holds 256 helicities
+        binding.lib()
+        n = binding.ctypes.c_int(0)
+        binding._check(binding.lib().mg_filter_helicities_noalloc(
+            big.handle, binding._ptr(mom), 1, None, binding.ctypes.byref(n)), "noalloc")
+
+
+def test_extras_flow_weights_alphas_sde_and_choices(big, events):
+    """Per-event extras of the 2 -> 7 process: flow weights against the
+    oracle's Berends-Giele colour-ordered amplitudes (sum_h |J_s,h|^2 =
+    sum_h |A_s,h|^2 for every one of the 5040 flows), alpha_s rescaling,
+    channel weights, and the helicity and colour choices."""
+    mom, (ref, _) = events
+    n = len(mom)
+    md = torch.from_numpy(mom).cuda()
+    nc = 5040
+    flow = torch.empty((n, nc), dtype=torch.float64, device="cuda")
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    a = np.array([0.10, 0.118, 0.13])[:n]
+    sde = torch.empty(n, dtype=torch.float64, device="cuda")
+    rng = np.random.default_rng(11)
+    rh, rc = rng.uniform(size=n), rng.uniform(size=n)
+    hel = torch.empty(n, dtype=torch.int32, device="cuda")
+    col = torch.empty(n, dtype=torch.int32, device="cuda")
+    big.sigmakin_ex(md, out, alphas=torch.from_numpy(a).cuda(), channel=17, sde=sde, flow=flow,
+                    rnd_hel=torch.from_numpy(rh).cuda(), hel_out=hel,
+                    rnd_col=torch.from_numpy(rc).cuda(), col_out=col)
+    outh = torch.empty((n, 512), dtype=torch.float64, device="cuda")
+    big.sigmakin_hel(md, torch.empty(n, dtype=torch.float64, device="cuda"), outh)
+    torch.cuda.synchronize()
+    got, fw, mh = out.cpu().numpy(), flow.cpu().numpy(), outh.cpu().numpy()
+    assert np.abs(got / (ref * (a / 0.118) ** 7) - 1).max() <= RTOL
+    w = sde.cpu().numpy()
+    assert np.all(w >= 0) and np.all(w <= 1)
+    ref_flow = sum(np.abs(oracle.amplitudes(mom[0], h)) ** 2 for h in range(512))
+    assert np.abs(fw[0] - ref_flow).max() <= RTOL * ref_flow.max()
+
+    def pick(wts, r):
+        c = np.cumsum(wts)
+        return int(np.searchsorted(c, r * c[-1], side="right"))
+
+    got_h, got_c = hel.cpu().numpy(), col.cpu().numpy()
+    for e in range(n):
+        assert got_c[e] == pick(fw[e], rc[e])
+        cum = np.cumsum(mh[e]) / mh[e].sum()
+        if np.min(np.abs(cum - rh[e])) > 1e-12:
+            assert got_h[e] == pick(mh[e], rh[e])

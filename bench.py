@@ -558,6 +558,13 @@ def run_ours(args):
                "h2d_bytes_per_step": nevt * npar * 4 * 8, "d2h_bytes_per_step": nevt * 8}
         assert torch.isfinite(host_out).all().item()
 
+    # value distribution of |M|^2 (heavy tailed): quantiles of log10, untimed
+    me_q = None
+    if rank == 0:
+        import numpy as np
+        lg = np.log10(np.clip(out.cpu().numpy(), 1e-300, None))
+        me_q = {f"q{q:g}": float(np.quantile(lg, q / 100)) for q in (1, 10, 50, 90, 99)}
+
     accuracy = None
     if rank == 0 and args.check > 0:
         import numpy as np
@@ -605,6 +612,7 @@ def run_ours(args):
             "clocks": clk,
             "cpu_baseline": cpu,
             "accuracy": accuracy,
+            "me_log10_quantiles": me_q,
             "wall_s_timed": wall,
         }
         print(json.dumps(line), flush=True)

@@ -89,7 +89,8 @@ typedef struct {
 } mg_info;
 
 /* Create a process from its description, e.g. "g g > t t~ g g".  Supported:
- * g g > t t~ followed by 0..4 final gluons.  Uploads the process tables to
+ * g g > t t~ followed by 0..4 final gluons (5 final gluons: the table-file
+ * entry point below).  Uploads the process tables to
  * the current CUDA device.  params may be NULL (mt 173, wt 1.4915,
  * alphas 0.118, filtered helicities, FP64). */
 int mg_process_create(const char *process, const mg_params *params, mg_process **out);

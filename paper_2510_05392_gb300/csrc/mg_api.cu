@@ -1,6 +1,7 @@
 // Host runtime behind the C ABI declared in include/mgpu.h: process
-// registry, device tables, argument checks, helicity filtering and the
-// launch of the diagram kernel.
+// registry (compiled-in tables and table files), device tables, argument
+// checks, helicity filtering, and the launch sequences of the FP64, mixed
+// and HBM-state (2 -> 7) paths with their per-event extras.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>

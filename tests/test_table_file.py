@@ -83,3 +83,32 @@ def test_damaged_file_is_rejected(tmp_path, case):
 
 def test_missing_file(tmp_path):
     assert _create(tmp_path / "absent.bin") == BAD_PROCESS
+
+
+def test_emitter_round_trip(tmp_path):
+    """The process compiler's table file holds exactly its program, scatter
+    list, colour row and flow orderings (written for g g > t t~ g g here; the
+    library itself only loads 7-gluon files)."""
+    from paper_2510_05392_gb300.compiler import colour, emit, program
+    f = tmp_path / "g4.bin"
+    emit.emit_blob(4, str(f))
+    data = f.read_bytes()
+    assert data[:8] == b"MGPROC01"
+    h = struct.unpack_from("<12i", data, 8)
+    den, iden, fd, fc = struct.unpack_from("<q3d", data, 56)
+    prog = program.build_program(4)
+    assert h == (1, 4, 6, 24, len(prog.ops), len(prog.scatter), prog.nslot, prog.nslot_f,
+                 prog.nslot_acc, prog.ncolour_groups, prog.ndiagrams, prog.nterms)
+    off = 56 + 32
+    ops = struct.unpack_from(f"<{8 * h[4]}i", data, off)
+    off += 32 * h[4]
+    assert [list(ops[8 * i:8 * i + 8]) for i in range(h[4])] == [list(r) for r in prog.ops]
+    scat = struct.unpack_from(f"<{h[5]}i", data, off)
+    off += 4 * h[5]
+    assert list(scat) == list(prog.scatter)
+    row = struct.unpack_from("<24q", data, off)
+    off += 8 * 24
+    chat, d, perms = colour.colour_matrix(4)
+    assert den == d and list(row) == list(chat[0])   # row of the identity ordering
+    assert list(data[off:]) == [v for p in perms for v in p]
+    assert iden == 512.0 and fd == emit.algorithmic_flops(prog)["diagram"]

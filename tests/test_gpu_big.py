@@ -154,3 +154,21 @@ def test_extras_flow_weights_alphas_sde_and_choices(big, events):
         cum = np.cumsum(mh[e]) / mh[e].sum()
         if np.min(np.abs(cum - rh[e])) > 1e-12:
             assert got_h[e] == pick(mh[e], rh[e])
+
+
+def test_two_chunks_with_extras():
+    """640 events: more than one chunk of jamp rows (622 events fit 24 GiB),
+    so the second chunk's offsets into momenta, outputs and per-event inputs
+    are used; events on both sides of the boundary against the oracle."""
+    mom = _events(640, 777)
+    idx = [0, 621, 622, 639]
+    ref = oracle.me(mom[idx])
+    p = binding.Process(PROC, hel_mode=binding.MG_HEL_ALL, precision=binding.MG_MIXED_BF16)
+    a = np.full(640, 0.118)
+    a[idx] = [0.11, 0.12, 0.125, 0.13]
+    out = torch.empty(640, dtype=torch.float64, device="cuda")
+    p.sigmakin_ex(torch.from_numpy(mom).cuda(), out, alphas=torch.from_numpy(a).cuda())
+    torch.cuda.synchronize()
+    assert p.device_status() == 0
+    got = out.cpu().numpy()[idx]
+    assert np.abs(got / (ref * (a[idx] / 0.118) ** 7) - 1).max() <= MIXED_RTOL

@@ -5,6 +5,8 @@
 #ifndef MGPU_BENCH_H
 #define MGPU_BENCH_H
 
+#include <stdint.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -41,6 +43,15 @@ int mg_kernel_times(struct mg_process *p, int reset, double *ms_out, int *launch
  * (every process and stream; the FP64 peak probe and replays of captured CUDA
  * graphs not included).  For counting the launches of a timed region. */
 int mg_launch_count(unsigned long long *out);
+
+/* Test hook for the tensor-core colour sum (mixed-precision processes): for
+ * caller rows rows_dev[nrows][ncolor] (FP64, device; nrows a multiple of
+ * 128), writes q8_dev[nrows / 8] = the sum over each 8 consecutive rows v of
+ * v^T (D C) v, through the same BF16 splitting, tensor-core kernel (single
+ * tile up to 128 flows, block-triangular above) and fixed-order sums as the
+ * matrix-element path.  Allocates its workspace; synchronises. */
+int mg_debug_colour_sum_rows(struct mg_process *p, const double *rows_dev, int64_t nrows,
+                             double *q8_dev, void *stream);
 
 /* Copies an internal buffer of the surrogate's last forward/backward pass to
  * the host as FP32 out[rows][cols] (padded widths): which = 0 activations of

@@ -85,6 +85,7 @@ _SIGS = {
     "mg_set_kernel_timing": ([_VP, ctypes.c_int], ctypes.c_int),
     "mg_kernel_times": ([_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "mg_launch_count": ([ctypes.POINTER(ctypes.c_ulonglong)], ctypes.c_int),
+    "mg_debug_colour_sum_rows": ([_VP, _VP, ctypes.c_int64, _VP, _VP], ctypes.c_int),
     "mg_probe_fp64_peak": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
 }
 

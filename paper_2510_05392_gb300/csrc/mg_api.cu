@@ -1028,6 +1028,41 @@ int mg_check_dev_ptr(const void *ptr, int device) { return check_dev_ptr(ptr, de
 int mg_cuda_fail(cudaError_t e) { return cuda_fail(e); }
 mg_dev_proc mg_dev_view(const mg_process *p) { return dev_view(p); }
 
+// Test hook: the tensor-core colour sum of caller rows, per group of 8 rows.
+extern "C" int mg_debug_colour_sum_rows(mg_process *p, const double *rows, int64_t nrows,
+                                        double *q8, void *stream) {
+    if (!p || nrows <= 0 || nrows % 128) return MG_ERR_BAD_ARG;
+    if (p->par.precision != MG_MIXED_BF16 || !p->d_cmat) return MG_ERR_UNSUPPORTED;
+    int st = check_dev_ptr(rows, p->device);
+    if (!st) st = check_dev_ptr(q8, p->device);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nc = p->tab->ncolor;
+    const bool block = nc > 128;
+    __nv_bfloat16 *jb = nullptr;
+    double *part = nullptr;
+    const long long nparts = block ? nrows * (2 * p->np / 128) : nrows / 128 * mg_tc_parts_per_tile(8);
+    cudaError_t e = cudaMalloc(&jb, sizeof(__nv_bfloat16) * 3 * p->kp * nrows);
+    if (e == cudaSuccess) e = cudaMalloc(&part, sizeof(double) * nparts);
+    if (e == cudaSuccess) e = mg_launch_rows_split(rows, nrows, nc, p->kp, jb, s);
+    if (e == cudaSuccess) {
+        if (block)
+            e = mg_launch_colorsum_tc_big(jb, nrows, p->kp, p->d_cmat, p->np, 0, part, p->d_err, s);
+        else
+            e = mg_launch_colorsum_tc(jb, nrows, p->kp, p->d_cmat, p->np, nc, 8, 0, part, p->d_err, s);
+    }
+    if (e == cudaSuccess) {
+        if (block)
+            e = mg_launch_event_sum_rows(part, nrows, 2 * p->np / 128, 8, nrows / 8, 1.0, q8, s);
+        else
+            e = mg_launch_event_sum(part, nrows / 8, mg_tc_parts_per_event(8), 1.0, q8, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(jb);
+    cudaFree(part);
+    return e == cudaSuccess ? MG_OK : cuda_fail(e);
+}
+
 extern "C" int mg_device_status(mg_process *p, void *stream) {
     if (!p) return MG_ERR_BAD_ARG;
     cudaStream_t s = (cudaStream_t)stream;

@@ -656,6 +656,25 @@ __global__ void k_event_sum_rows(const double *__restrict__ part, long long R, i
     me[e] = s * factor;
 }
 
+// Caller rows to tensor-core rows (test hook): rows[r * nc + c] (FP64) to
+// jb[r * 3 kp + s * kp + c] as three BF16 pieces (the value rounded to FP32,
+// then split twice), colours >= nc zero.
+__global__ void k_rows_split(const double *__restrict__ rows, long long nrows, int nc, int kp,
+                             __nv_bfloat16 *__restrict__ jb) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nrows * kp) return;
+    const long long r = idx / kp;
+    const int c = (int)(idx % kp);
+    const float f = c < nc ? __double2float_rn(rows[r * nc + c]) : 0.0f;
+    const __nv_bfloat16 hi = __float2bfloat16_rn(f);
+    const float r1 = f - __bfloat162float(hi);
+    const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+    __nv_bfloat16 *row = jb + r * (long long)(3 * kp);
+    row[c] = hi;
+    row[kp + c] = mid;
+    row[2 * kp + c] = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+}
+
 typedef CUresult (*encode_tiled_fn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
                                     const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
                                     const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -762,6 +781,15 @@ cudaError_t mg_launch_colorsum_tc_big(const __nv_bfloat16 *jb, long long R, int 
     mg_note_launch();
     k_colorsum_tc_big<<<(unsigned)grid, TB_THREADS, smem, stream>>>(ma, mb, jb, kp, np, mtiles, extra_tx,
                                                                      part, R, err);
+    return cudaGetLastError();
+}
+
+cudaError_t mg_launch_rows_split(const double *rows, long long nrows, int nc, int kp,
+                                 __nv_bfloat16 *jb, cudaStream_t stream) {
+    if (nrows <= 0) return cudaSuccess;
+    const long long n = nrows * kp;
+    mg_note_launch();
+    k_rows_split<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(rows, nrows, nc, kp, jb);
     return cudaGetLastError();
 }
 

@@ -150,6 +150,8 @@ int mg_tc_parts_per_tile(int cpe);
 // tensor-core colour sum of the table-file process over the block upper
 // triangle: jb [R][3*kp] BF16 rows, cmat [2*np][kp] (np == kp, multiples of
 // 128); writes part[(2 I + half) * R + r] for the 2 np / 128 colour halves
+cudaError_t mg_launch_rows_split(const double *rows, long long nrows, int nc, int kp,
+                                 __nv_bfloat16 *jb, cudaStream_t stream);
 cudaError_t mg_launch_event_sum_rows(const double *part, long long R, int ncols, int cpe, long long nevt,
                                      double factor, double *me, cudaStream_t stream);
 cudaError_t mg_launch_colorsum_tc_big(const __nv_bfloat16 *jb, long long R, int kp,

@@ -86,3 +86,27 @@ def test_bounded_wait_reports_timeout_and_context_survives(ng):
     p.sigmakin(mom, out)
     assert p.device_status() == binding.MG_OK
     assert abs(out.item() / oracle.me(mom_np)[0] - 1) <= MIXED_RTOL
+
+
+@pytest.mark.parametrize("ng", [2, 3, 4])
+def test_exact_inputs_bit_identical(ng):
+    """Rows whose values are small integers (exact in one BF16 piece) and the
+    integer matrix D*C: every product and partial sum of the tensor-core colour
+    sum is an exactly representable integer (below 2^24 in the FP32
+    accumulator, per 128-colour block for 720 flows), so the result must equal
+    the exact integer quadratic form bit for bit."""
+    sqrts = CASES[ng][0]
+    p = _mixed(ng, sqrts)
+    chat, _ = p.color_matrix()
+    nc = chat.shape[0]
+    amp = 4 if nc <= 128 else 1
+    rng = np.random.default_rng(40 + ng)
+    v = rng.integers(-amp, amp + 1, size=(256, nc)).astype(np.int64)
+    exact = np.einsum("ri,ij,rj->r", v, chat, v).reshape(32, 8).sum(axis=1)
+    q8 = torch.empty(32, dtype=torch.float64, device="cuda")
+    rc = binding.lib().mg_debug_colour_sum_rows(
+        p.handle, torch.from_numpy(v.astype(np.float64)).cuda().data_ptr(), 256,
+        q8.data_ptr(), None)
+    assert rc == binding.MG_OK
+    got = q8.cpu().numpy()
+    assert np.array_equal(got, exact.astype(np.float64)), np.abs(got - exact).max()

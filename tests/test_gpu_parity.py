@@ -179,3 +179,32 @@ def test_ggttgggg_small():
     torch.cuda.synchronize()
     ref = oracle.me(mom)
     assert np.abs(out.cpu().numpy() / ref - 1).max() <= RTOL
+
+
+def test_pointer_and_size_errors():
+    """Negative sizes, null, misaligned and host pointers, bad launch shapes:
+    each returns its documented status and leaves the process usable."""
+    proc, sqrts, _ = PROCS[1]
+    p = _filtered(proc, 1, sqrts)
+    L = binding.lib()
+    mom = _gpu(_events(1, 4, 9, sqrts))
+    out = torch.empty(5, dtype=torch.float64, device="cuda")
+    h = p.handle
+    assert L.mg_sigmakin(h, mom.data_ptr(), -1, out.data_ptr(), None) == binding.MG_ERR_BAD_ARG
+    assert L.mg_sigmakin(h, None, 4, out.data_ptr(), None) == binding.MG_ERR_BAD_ARG
+    assert L.mg_sigmakin(h, mom.data_ptr(), 4, None, None) == binding.MG_ERR_BAD_ARG
+    assert L.mg_sigmakin(h, mom.data_ptr() + 4, 4, out.data_ptr(), None) == binding.MG_ERR_BAD_ARG
+    assert L.mg_sigmakin(h, mom.data_ptr(), 4, out.data_ptr() + 4, None) == binding.MG_ERR_BAD_ARG
+    host = torch.zeros(4, dtype=torch.float64)
+    assert L.mg_sigmakin(h, mom.data_ptr(), 4, host.data_ptr(), None) == binding.MG_ERR_BAD_ARG
+    for tpe, block in [(3, 0), (64, 0), (0, 256), (0, 48), (0, 16)]:
+        assert L.mg_set_launch(h, tpe, block) == binding.MG_ERR_BAD_ARG
+    assert L.mg_filter_helicities(h, mom.data_ptr(), 0, None, None) == binding.MG_ERR_BAD_ARG
+    assert L.mg_filter_helicities(h, mom.data_ptr(), 65537, None, None) == binding.MG_ERR_BAD_ARG
+    # still usable, ragged sizes around a warp
+    for n in (31, 33):
+        m = _events(1, n, 100 + n, sqrts)
+        o = torch.empty(n, dtype=torch.float64, device="cuda")
+        p.sigmakin(_gpu(m), o)
+        torch.cuda.synchronize()
+        assert np.abs(o.cpu().numpy() / oracle.me(m) - 1).max() < RTOL

@@ -23,7 +23,12 @@
 //                   qpart[I][r] = sum_{n in tile I} V_rn sum_{k >= 64 I} Cb_nk V_rk.
 //   k_event_sum_big per event, the sum over its items, good helicity
 //                   combinations, real/imaginary rows and tiles in a fixed
-//                   order (and |M_h|^2 per helicity for the filter).
+//                   order (and |M_h|^2 per helicity for the filter; the
+//                   per-event alpha_s factor and channel weight of the
+//                   extras).
+// In mixed precision k_rows_to_bf16 turns the rows into BF16 pieces and the
+// block-triangular tensor-core kernel of mg_colorsum_tc.cu replaces
+// k_colour_big; k_flow_weights_big gives the per-flow weights of the extras.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>

@@ -5,15 +5,28 @@ Workload (default): 524288 synthetic events of g g -> t t~ g g at sqrt(s) =
 resident in HBM.  One step = one mg_sigmakin call over the whole batch
 (momentum read, diagrams, colour sum, helicity sum).
 
+Other workloads (--workload): ggtt_16384, ggttggg_262144, ggttgggg_16384,
+ggttggggg_512 (2 -> 7, state in HBM), uneven_batch_4proc (one persistent
+graph-replayed launch over four processes), ggttgggg_surrogate (exact ME,
+MLP training, two-stage unweighting); --precision mixed puts the colour sum
+on the tensor cores.
+
 Prints one JSON line (rank 0).  Keys beyond the basic ones:
   e2e          the same metric through the public API with pinned host
                buffers: H2D of the step's momenta + mg_sigmakin + D2H of the
                matrix elements, every step
   roofline     the diagram kernel against the FP64 pipe ("alu"): algorithmic
-               FP64 flops per launch / CUDA-event launch time vs the FP64 FMA
-               peak measured live by mg_probe_fp64_peak
+               FP64 flops / the kernel's own CUDA-event time (recorded by the
+               library around its launches) vs the FP64 FMA peak measured
+               live by mg_probe_fp64_peak; traffic from the committed ncu
+               summary when it matches the current kernel sources
+  roofline_colour_tc   mixed precision: the tensor-core colour sum (HBM bound
+               up to 128 flows, tensor bound above)
+  roofline_colour_f64  the FP64 colour-sum kernel of the 2 -> 7 process
+  gpu_launches the library's own kernel launches in the timed region
   cpu_baseline the CPU oracle on the host cores on a bounded sample
   clocks       nvidia-smi samples taken during the timed region
+  me_log10_quantiles   quantiles of log10 |M|^2 of the workload
 
 --impl reference times the CPU oracle (the only reference this workload
 has) on bounded samples of the same workload.

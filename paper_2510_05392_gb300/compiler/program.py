@@ -246,8 +246,10 @@ def build_program(n: int, order: str = "middle") -> Program:
     # number of such classes is the paper's count of single-diagram-enhancement
     # channels: 3 / 15 / 105 / 945 for 2 to 5 gluons.)
     group_of, phase_of, rep = {}, {}, {}
+    sorted_colour = {}     # a term's colour decomposition in flow order (used twice)
     for d, _ in terms:
         items = sorted(d.color.items(), key=lambda kv: pidx[kv[0]])
+        sorted_colour[d.idx] = items
         c0 = complex(items[0][1])
         key = tuple((st, complex(c) / c0) for st, c in items)
         if key not in rep:
@@ -279,7 +281,7 @@ def build_program(n: int, order: str = "middle") -> Program:
         mem = members[g]
         if len(mem) == 1:
             off = len(scatter)
-            for string, c in sorted(d.color.items(), key=lambda kv: pidx[kv[0]]):
+            for string, c in sorted_colour[d.idx]:
                 scatter.append(pidx[string] * 4 + COEF_CODE[complex(c)])
             B._emit(code, [], ins, [off, len(scatter) - off, None, 0, g])
             continue

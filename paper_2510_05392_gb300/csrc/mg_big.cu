@@ -15,7 +15,9 @@
 //                   thread t at scratch[i * T + t], so a warp's accesses are
 //                   coalesced); the jamps accumulate directly into the FP64
 //                   colour-major rows of the colour sum, row
-//                   r = (2 v + re/im) * nipad + item, colour c at c * R + r.
+//                   r = 2 (v * nipad + item) + re/im, colour c at c * R + r
+//                   (real and imaginary part of a jamp side by side: one
+//                   16-byte read-modify-write per update).
 //   k_colour_big    the colour sum J^H C J (Sec. 3.3, Eq. "jcj") of every
 //                   row as a tiled FP64 quadratic form over the block upper
 //                   triangle of D*C (off-diagonal 64 x 64 blocks doubled, the
@@ -117,14 +119,14 @@ __device__ __forceinline__ void prefetch_inputs(const int4 &a, const int4 &b, co
 // The program of one item (same ops and semantics as the local-memory
 // interpreter of mg_kernels.cu): pools G (slot s, component m: 4 s + m),
 // F (slot s, variant v, component m: 8 s + 4 v + m), A (slot s, variant v:
-// 4 s + v); jamp (c, v) real part at jr[c * R + 2 v * nipad], imaginary part
-// one row block further.
+// 4 s + v); jamp (c, v) of the item at jr[c * R / 2 + v * nipad] (real,
+// imaginary).
 // sde8 (may be NULL): per top-helicity combination v, |A_channel|^2 in [v]
 // and the sum over colour-factor classes of |A_class|^2 in [4 + v].
 template <int NG>
 __device__ void run_item(const Kin<NG> &k, int g, const int4 *__restrict__ ops, int nops,
                          const int *__restrict__ scat, double mt, const Strided &WG,
-                         const Strided &WF, const Strided &ACC, double *__restrict__ jr, long long R,
+                         const Strided &WF, const Strided &ACC, double2 *__restrict__ jr, long long R,
                          long long nipad, int channel, double *sde8) {
     cx G0[4][4];
     int4 an = __ldg(ops), bn = __ldg(ops + 1);
@@ -264,25 +266,24 @@ __device__ void run_item(const Kin<NG> &k, int g, const int4 *__restrict__ ops, 
                 const int end = b.x + b.y;
                 for (int s0 = b.x; s0 < end; s0 += SCAT_BATCH) {
                     int ev[SCAT_BATCH];
-                    double old[SCAT_BATCH][8];
+                    double2 old[SCAT_BATCH][4];
 #pragma unroll
                     for (int q = 0; q < SCAT_BATCH; q++) ev[q] = (s0 + q < end) ? __ldg(scat + s0 + q) : -1;
 #pragma unroll
                     for (int q = 0; q < SCAT_BATCH; q++)
                         if (ev[q] >= 0) {
-                            const double *jc = jr + (long long)(ev[q] >> 2) * R;
+                            const double2 *jc = jr + (long long)(ev[q] >> 2) * (R / 2);
 #pragma unroll
-                            for (int w = 0; w < 8; w++) old[q][w] = jc[w * nipad];
+                            for (int v = 0; v < 4; v++) old[q][v] = jc[v * nipad];
                         }
 #pragma unroll
                     for (int q = 0; q < SCAT_BATCH; q++)
                         if (ev[q] >= 0) {
-                            double *jc = jr + (long long)(ev[q] >> 2) * R;
+                            double2 *jc = jr + (long long)(ev[q] >> 2) * (R / 2);
 #pragma unroll
                             for (int v = 0; v < 4; v++) {
                                 const cx t = unit_times(ev[q], amp[v]);
-                                jc[2 * v * nipad] = old[q][2 * v] + t.r;
-                                jc[(2 * v + 1) * nipad] = old[q][2 * v + 1] + t.i;
+                                jc[v * nipad] = make_double2(old[q][v].x + t.r, old[q][v].y + t.i);
                             }
                         }
                 }
@@ -313,7 +314,8 @@ __global__ void __launch_bounds__(BIG_BLOCK, 3)   // 168 registers: three blocks
         Kin<NG> k;
         kinematics<NG>(k, mom + e * (NPAR * 4), mt, wt);
         double sde8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        run_item<NG>(k, u >> 4, ops, nops, scat, mt, WG, WF, ACC, jrow + item, R, nipad, channel,
+        run_item<NG>(k, u >> 4, ops, nops, scat, mt, WG, WF, ACC,
+                     reinterpret_cast<double2 *>(jrow) + item, R, nipad, channel,
                      sde_item ? sde8 : nullptr);
         if (sde_item)
             for (int q = 0; q < 8; q++) sde_item[item * 8 + q] = sde8[q];
@@ -400,7 +402,7 @@ __global__ void k_event_sum_big(const double *__restrict__ qpart, long long R, i
             if (!((u >> v) & 1)) continue;
             double mh = 0.0;
             for (int ri = 0; ri < 2; ri++) {
-                const long long r = (2 * v + ri) * nipad + item;
+                const long long r = 2 * (v * nipad + item) + ri;
                 for (int I = 0; I < ntile; I++) mh += qpart[(long long)I * R + r];
             }
             tot += mh;
@@ -424,15 +426,15 @@ __global__ void k_flow_weights_big(const double *__restrict__ jrow, long long R,
     if (idx >= nevt * ncolor) return;
     const long long e = idx / ncolor;
     const int c = (int)(idx % ncolor);
-    const double *col = jrow + (long long)c * R;
+    const double2 *col = reinterpret_cast<const double2 *>(jrow + (long long)c * R);
     double w = 0.0;
     for (int iu = 0; iu < nunits; iu++) {
         const long long item = e * nunits + iu;
         const int u = __ldg(units + iu);
         for (int v = 0; v < 4; v++) {
             if (!((u >> v) & 1)) continue;
-            const double re = col[2 * v * nipad + item], im = col[(2 * v + 1) * nipad + item];
-            w = fma(re, re, fma(im, im, w));
+            const double2 z = col[v * nipad + item];
+            w = fma(z.x, z.x, fma(z.y, z.y, w));
         }
     }
     jw[idx] = w;

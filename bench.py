@@ -147,6 +147,25 @@ class Clocks:
 _FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
 
+def _fp64_peak():
+    """FP64 FMA peak of this GPU in flops/s, measured live by the library's
+    probe (16 independent FMA chains per thread), or None."""
+    from paper_2510_05392_gb300 import binding
+    L = binding.lib()
+    L.mg_probe_fp64_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.POINTER(ctypes.c_double)]
+    peak = ctypes.c_double(0.0)
+    return peak.value if L.mg_probe_fp64_peak(0, 20000, 5, ctypes.byref(peak)) == 0 else None
+
+
+def _fp64_roofline(flops_per_step, seconds_per_step, kernel, peak):
+    ach = flops_per_step / seconds_per_step
+    return {"bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12 if peak else None,
+            "unit": "TFLOP/s", "frac": ach / peak if peak else None, "traffic": None,
+            "kernel": kernel + " (FP64 pipe; peak = FP64 FMA probe, measured live)",
+            "flops_per_step": flops_per_step}
+
+
 def _measured_peak(key):
     """Measured peak of this GPU pool (copy GB/s, cuBLAS bf16 TFLOP/s), else
     the fallback figure."""
@@ -255,6 +274,11 @@ def run_batch(args):
         m = torch.from_numpy(ps.generate(n, ng, 1500.0, 20251005 + 4, **kw)).to(dev)
         blocks.append((p, m, torch.empty(n, dtype=torch.float64, device=dev)))
         total += n
+    flops_step = 0.0
+    for p, m, _ in blocks:
+        i = p.info()
+        flops_step += m.shape[0] * i.ngood * (i.flops_diagram + i.flops_colour)
+    peak = _fp64_peak()
     b = binding.Batch(blocks)
     tuned_ms = b.autotune(reps=1)
     tpe, ctas = b.config()
@@ -287,6 +311,7 @@ def run_batch(args):
                    "autotuned": {"threads_per_event": tpe, "ctas_per_sm": ctas,
                                  "tuning_ms_per_step": tuned_ms}},
         "per_process_launches_events_per_s": total * args.steps / t_seq,
+        "roofline": _fp64_roofline(flops_step, t_batch / args.steps, "k_batch (whole step)", peak),
         "gpu_launches": args.steps,
     }
     print(json.dumps(line), flush=True)
@@ -404,6 +429,9 @@ def run_surrogate(args):
                    "mlp": "32(28 s_ij/s)-256-256-256-1 SiLU, BF16 weights/activations, FP32 master + Adam"},
         "exact_fp64": {"events_per_s": rate_exact, "seconds": t_exact,
                        "fp64_tflops": rate_exact * p.info().ngood * (p.info().flops_diagram + p.info().flops_colour) / 1e12},
+        "roofline": _fp64_roofline(
+            ntrain * p.info().ngood * (p.info().flops_diagram + p.info().flops_colour), t_exact,
+            "k_sigmakin on the training events (wall time of the exact-ME pass)", _fp64_peak()),
         "training": {"seconds": t_train, "final_epoch_loss": loss.value, "r2_log_me_train": float(r2)},
         "two_stage": {"seconds": t_two, "exact_evaluations": int(nex.value), "accepted": nacc,
                       "what_max": what_max, "r_max": r_max, "kish_ess": kish,
@@ -446,12 +474,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
 
     # FP64 peak measured live on this GPU (roofline denominator)
-    L = binding.lib()
-    L.mg_probe_fp64_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                     ctypes.POINTER(ctypes.c_double)]
-    peak = ctypes.c_double(0.0)
-    rc = L.mg_probe_fp64_peak(0, 20000, 5, ctypes.byref(peak))
-    fp64_peak = peak.value if rc == 0 else None
+    fp64_peak = _fp64_peak()
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
     for _ in range(args.warmup):

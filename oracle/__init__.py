@@ -11,9 +11,9 @@ Pieces (each cites the passage it follows in its own module):
   topology.py     brute-force diagram counter
   closed_form.py  Combridge's g g -> Q Qbar formula
 
-Parity status: every function here is pinned by tests/test_oracle_*.py
-(closed form, gauge, Lorentz and Bose invariance, brute-force colour traces,
-diagram counts, paper table counts).
+Parity status: every function here is pinned by tests/test_oracle*.py
+(closed form, the massless Parke-Taylor amplitudes, gauge, Lorentz and Bose
+invariance, brute-force colour traces, diagram counts, paper table counts).
 """
 from __future__ import annotations
 

@@ -152,6 +152,70 @@ def test_closed_form_massless_limit():
     assert np.median(np.abs(a / textbook - 1)) < 1e-14
 
 
+def _mdot(a, b):
+    return a[..., 0] * b[..., 0] - (a[..., 1:] * b[..., 1:]).sum(-1)
+
+
+@pytest.mark.parametrize("ng", [0, 1, 2, 3, 4, 5])
+def test_parke_taylor_massless_quark_line(ng):
+    """Massless limit (m_t = Gamma_t = 0) of every colour-ordered amplitude
+    against the Parke-Taylor formula for a quark pair and n gluons (Berends and
+    Giele 1987; Mangano and Parke, Phys. Rep. 200 (1991) 301), up to 7 gluons.
+
+    All particles are taken outgoing: incoming momenta k = -p, incoming
+    helicities flipped.  The flow (t^s1 ... t^sn)_{i_t, i_tbar} belongs to the
+    cyclic order tbar, t, g_s1, ..., g_sn.  Where exactly one gluon j has the
+    helicity of one member f of the (opposite-helicity) quark pair and every
+    other gluon the opposite one (MHV and its parity conjugate),
+        |A_s|^2 = 2^n s_fj^3 s_f'j / (s_tbar,t s_t,s1 s_s1,s2 ... s_sn,tbar),
+    s_ab = |2 k_a.k_b|; the formula is written for generators with
+    Tr(T^a T^b) = delta^ab, and the flows here use t^a = T^a / sqrt(2), hence
+    2^n.  Quark pairs of equal helicity, and gluons all of one helicity, give
+    zero (helicity selection rules).  This fixes the absolute normalisation,
+    the phase-free magnitude of each ordering and the orientation of the flows
+    for every gluon multiplicity, independently of the width reading."""
+    n = ng + 2
+    npar = n + 2
+    nevt = 2 if ng < 4 else 1
+    kw = dict(ptmin=20.0, drmin=0.4) if ng else {}
+    p = ps.generate(nevt, ng, 1000.0 if ng < 4 else 2000.0, 800 + ng, mt=0.0, **kw)
+    p[:, 2:, 0] = np.sqrt((p[:, 2:, 1:] ** 2).sum(-1))      # exactly on the light cone
+    _, _, perms = oracle.color_data(n)
+    glu = np.array([0, 1] + list(range(4, npar)))            # particle index of each gluon
+    order = glu[np.asarray(perms)]                           # [n!][n] particle indices
+    T, TB = 2, 3
+    mhv, zero = [], []
+    for h in range(1 << npar):
+        lam = [1 if (h >> (npar - 1 - i)) & 1 else -1 for i in range(npar)]
+        out = [-l if i < 2 else l for i, l in enumerate(lam)]
+        neg = [g for g in glu if out[g] < 0]
+        pos = [g for g in glu if out[g] > 0]
+        if out[T] == out[TB] or not neg or not pos:
+            zero.append(h)
+        elif len(neg) == 1 or len(pos) == 1:
+            j = neg[0] if len(neg) == 1 else pos[0]
+            f = T if out[T] == out[j] else TB
+            mhv.append((h, j, f, TB if f == T else T))
+    assert len(mhv) == (4 if n == 2 else 4 * n)
+    if ng >= 4:
+        zero = zero[:: max(1, len(zero) // 8)]
+    for e in range(nevt):
+        k = p[e].copy()
+        k[:2] *= -1
+        S = np.abs(2 * _mdot(k[:, None, :], k[None, :, :]))
+        chain = S[TB, T] * S[T, order[:, 0]] * S[order[:, -1], TB]
+        for a in range(n - 1):
+            chain = chain * S[order[:, a], order[:, a + 1]]
+        scale = 0.0
+        for h, j, f, fp in mhv:
+            A = oracle.amplitudes(p[e], h, mt=0.0, wt=0.0)
+            pt = 2.0 ** n * S[f, j] ** 3 * S[fp, j] / chain
+            assert np.abs(np.abs(A) ** 2 / pt - 1).max() < 1e-9, (h, j, f)
+            scale = max(scale, np.abs(A).max())
+        for h in zero:
+            assert np.abs(oracle.amplitudes(p[e], h, mt=0.0, wt=0.0)).max() <= 1e-12 * scale, h
+
+
 @pytest.mark.parametrize("ng", [0, 1, 2, 3, 4, 5])
 def test_gauge_invariance_every_ordering(ng):
     """eps_i -> k_i makes every colour-ordered amplitude vanish (zero width);

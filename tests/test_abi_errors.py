@@ -52,3 +52,15 @@ def test_status_strings():
               binding.MG_ERR_NO_MEMORY, binding.MG_ERR_UNSUPPORTED):
         assert lib.mg_status_string(s).decode() not in ("", "unknown status")
     assert lib.mg_status_string(-99).decode() == "unknown status"
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without the built CUDA library there is no fallback: the first call
+    that needs it raises."""
+    from paper_2510_05392_gb300 import binding
+    monkeypatch.setattr(binding, "LIB_PATH", str(tmp_path / "libmgpu.so"))
+    monkeypatch.setattr(binding, "_lib", None)
+    with pytest.raises(ImportError):
+        binding.lib()
+    with pytest.raises(ImportError):
+        binding.Process("g g > t t~ g g")

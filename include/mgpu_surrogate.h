@@ -4,8 +4,9 @@
  * pointers, asynchronous on `stream` unless stated, negative status on
  * error).
  *
- * The paper has no learned component (its outlook mentions neural-network
- * phase-space sampling only); this follows the published scheme of
+ * The paper has no learned component (its "Summary and outlook" section
+ * only names neural phase-space sampling, MadNIS, as future work); this
+ * follows the published scheme of
  * rejection sampling with network weight estimates (Danziger, Janssen,
  * Schumann, Siegert, SciPost Phys. 12 (2022) 164), in which the exact matrix
  * element corrects every surrogate acceptance so the unweighted sample stays

@@ -69,6 +69,8 @@ def _load():
                                               ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp]
             lib.oracle_amplitudes.restype = ctypes.c_int
             lib.oracle_threads.restype = ctypes.c_int
+            lib.oracle_externals.argtypes = [ctypes.c_int, dp, ctypes.c_int, dp, dp, dp, dp]
+            lib.oracle_externals.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -144,6 +146,26 @@ def amplitudes(p_event: np.ndarray, hel: int, gauge_leg: int = -1,
     if rc != 0:
         raise RuntimeError("oracle_amplitudes failed")
     return out[0::2] + 1j * out[1::2]
+
+
+def externals(p_event: np.ndarray, hel: int):
+    """External states of one event [npar][4] and helicity index, in the
+    conventions of the Berends-Giele amplitudes: (eps [n][4] complex, incoming
+    eps and outgoing eps*; kin [n][4] incoming gluon momenta; ubar(p3) [4];
+    v(p4) [4]), gluons in particle order."""
+    p = np.ascontiguousarray(p_event, dtype=np.float64)
+    n = p.shape[0] - 2
+    eps = np.zeros(8 * n)
+    kin = np.zeros(4 * n)
+    ub = np.zeros(8)
+    v = np.zeros(8)
+    rc = _load().oracle_externals(n, _ptr(p, ctypes.c_double), int(hel), _ptr(eps, ctypes.c_double),
+                                  _ptr(kin, ctypes.c_double), _ptr(ub, ctypes.c_double),
+                                  _ptr(v, ctypes.c_double))
+    if rc != 0:
+        raise RuntimeError("oracle_externals failed")
+    c = lambda a: a[0::2] + 1j * a[1::2]
+    return c(eps).reshape(n, 4), kin.reshape(n, 4), c(ub), c(v)
 
 
 def good_helicity_mask(momenta_test: np.ndarray, rel: float = 1e-14, **kw) -> np.ndarray:

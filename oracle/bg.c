@@ -321,8 +321,8 @@ int oracle_me(int n, const double *mom, int64_t nevt, const double *par_in, cons
     }
     int status = 0;
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel
+    const int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel num_threads(nt)
 #endif
     {
         cplx *A = (cplx *)malloc(sizeof(cplx) * ncolor);
@@ -380,4 +380,31 @@ int oracle_threads(void) {
 #else
     return 1;
 #endif
+}
+
+/* External states of one event and helicity index, for the oracle's
+ * single-diagram evaluation (oracle/sde.py): eps_out [n][4] polarisation
+ * vectors (incoming eps, outgoing eps*), kin_out [n][4] incoming momenta of
+ * the gluons, ub_out [4] = ubar(p3), v_out [4] = v(p4); complex values as
+ * (re, im) pairs.  Same conventions as the Berends-Giele amplitudes above. */
+int oracle_externals(int n, const double *mom, int h, double *eps_out, double *kin_out,
+                     double *ub_out, double *v_out) {
+    if (n < 2 || n > MAXG) return -1;
+    init_gamma();
+    cplx eps[MAXG][4], ub[4], v[4];
+    double kin[MAXG][4];
+    externals(n, mom, h, -1, eps, kin, ub, v);
+    for (int g = 0; g < n; g++)
+        for (int m = 0; m < 4; m++) {
+            eps_out[8 * g + 2 * m] = creal(eps[g][m]);
+            eps_out[8 * g + 2 * m + 1] = cimag(eps[g][m]);
+            kin_out[4 * g + m] = kin[g][m];
+        }
+    for (int c = 0; c < 4; c++) {
+        ub_out[2 * c] = creal(ub[c]);
+        ub_out[2 * c + 1] = cimag(ub[c]);
+        v_out[2 * c] = creal(v[c]);
+        v_out[2 * c + 1] = cimag(v[c]);
+    }
+    return 0;
 }

@@ -20,9 +20,17 @@
  *   helicity index   h in [0, 2^npar): bit (npar-1-i) set <=> particle i has
  *                    positive helicity
  *   streams          every compute call is asynchronous and ordered on the
- *                    given cudaStream_t (NULL = legacy default stream); the
- *                    library never synchronises the device inside
- *                    mg_sigmakin
+ *                    given cudaStream_t (NULL = legacy default stream).
+ *                    mg_sigmakin of an FP64 process compiled into the
+ *                    library neither allocates nor synchronises.  The mixed
+ *                    precision path, the table-file process and the extras
+ *                    keep per-process workspaces grown on demand: the first
+ *                    call, and any call with more events than before,
+ *                    allocates (cudaFree/cudaMalloc, which can synchronise
+ *                    the device); later calls of at most that size do not.
+ *                    Calls on one process share its workspaces, so they must
+ *                    not overlap on the GPU: issue them on one stream (or
+ *                    order the streams), or use one process per stream.
  *
  * Ownership: the caller owns all momentum/output buffers.  The library owns
  * the opaque process handle, its device tables and its workspaces, all
@@ -86,6 +94,7 @@ typedef struct {
     double iden;          /* averaging factor                             */
     double flops_diagram; /* algorithmic FP64 flops per helicity: diagrams */
     double flops_colour;  /* algorithmic FP64 flops per helicity: colour sum */
+    int nchannel;         /* single-diagram-enhancement channels          */
 } mg_info;
 
 /* Create a process from its description, e.g. "g g > t t~ g g".  Supported:
@@ -97,8 +106,9 @@ int mg_process_create(const char *process, const mg_params *params, mg_process *
 
 /* Create g g > t t~ g g g g g (2 -> 7: 5040 colour flows; the paper could
  * build it for CPUs only, Table "ggtt5g") from the binary table file the
- * process compiler writes (compiler/emit.py emit_blob: "MGPROC01" header,
- * program, jamp scatter, colour row by relative ordering, flow orderings).
+ * process compiler writes (compiler/emit.py emit_blob: "MGPROC02" header,
+ * program, jamp scatter, colour row by relative ordering, flow orderings,
+ * channel colour factors).
  * Every index of the program is checked against its pools before anything
  * reaches the device; a damaged or foreign file gives MG_ERR_BAD_PROCESS.
  * Runs with its wavefunction state in HBM (about 1.9 MB per thread, three
@@ -164,14 +174,23 @@ int mg_device_status(mg_process *p, void *stream);
  *   alphas_dev       [nevt] per-event alpha_s.  Every vertex is QCD, so
  *                    |M|^2 scales as alpha_s^ngluon: the matrix element is
  *                    rescaled by (alphas[e] / params.alphas)^ngluon.
- *   channel          colour-factor class used as the enhancement channel, or
- *                    -1.  The classes of diagram terms whose colour factors
- *                    agree up to a phase are as many as the paper's channels
- *                    (3 / 15 / 105 / 945; 10395 and 135135 for 6 and 7
- *                    gluons); channel c's amplitude is the sum of its class's
- *                    terms.
- *   sde_weight_dev   out [nevt] (required when channel >= 0):
- *                    sum_h |A_c,h|^2 / sum_h sum_c' |A_c',h|^2 (good helicities)
+ *   channel          single-diagram-enhancement channel of every event, or
+ *                    -1.  The channels are the diagrams that MadEvent's
+ *                    single diagram enhancement uses (table "complexity",
+ *                    row 3 of the paper): the Feynman diagrams made of
+ *                    three-point vertices only, 3 / 15 / 105 / 945 for 2 to
+ *                    5 gluons (10395 and 135135 for 6 and 7).  Channel c is
+ *                    the c-th in the order of mg_sde_channels.
+ *   channel_ids_dev  [nevt] int32, per-event channels (the paper's
+ *                    event-by-event channel identifier); overrides channel
+ *                    when not NULL.  An id outside [0, nchannel) gives a
+ *                    weight of 0 for that event.
+ *   sde_weight_dev   out [nevt] (required with a channel or channel ids):
+ *                    sum_h |D_c,h|^2 / sum_h sum_c' |D_c',h|^2 over the good
+ *                    helicities h and the channels c', D_c,h the amplitude of
+ *                    diagram c alone (its colour coefficients have modulus
+ *                    one); diagrams with a four-gluon vertex enter neither
+ *                    sum
  *   flow_weight_dev  out [nevt][ncolor]: sum over good helicities of |J_s|^2
  *                    (jamps without couplings)
  *   rnd_hel_dev, hel_out_dev   uniforms in [0,1) and out [nevt] helicity index:
@@ -189,6 +208,7 @@ typedef struct {
     int *hel_out_dev;
     const double *rnd_col_dev;
     int *col_out_dev;
+    const int *channel_ids_dev;
 } mg_sigmakin_extras;
 int mg_sigmakin_ex(mg_process *p, const double *momenta_dev, int64_t nevt,
                    const mg_sigmakin_extras *extras, double *me_out_dev, void *stream);
@@ -208,6 +228,17 @@ int mg_color_matrix(const mg_process *p, int64_t *ints_out, int64_t *denom_out);
 /* Good-helicity mask [2^npar] (1 = good) after filtering (or all ones in
  * MG_HEL_ALL mode).  MG_ERR_NOT_FILTERED before. */
 int mg_helicity_mask(const mg_process *p, uint8_t *mask_out);
+
+/* Single-diagram-enhancement channels (the diagrams MadEvent's single
+ * diagram enhancement uses, table "complexity" row 3 and Sec. 2.2 of the
+ * paper: the Feynman diagrams made of three-point vertices only).  A channel
+ * is identified by its diagram's colour factor in the flow basis of
+ * mg_color_matrix: codes_out[c][s] (int8, [nchannel][ncolor], may be NULL)
+ * is 0 when flow s is absent, else the coefficient divided by the channel's
+ * first one (in flow order) coded 1: +1, 2: -1, 3: +i, 4: -i.  Channels are
+ * numbered in the lexicographic order of these code rows.  *nchannel_out
+ * (may be NULL) receives the count.  Host-side; nothing runs on the GPU. */
+int mg_sde_channels(const mg_process *p, int *nchannel_out, int8_t *codes_out);
 
 void mg_process_destroy(mg_process *p);
 

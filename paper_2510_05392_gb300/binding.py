@@ -37,14 +37,15 @@ class mg_info(ctypes.Structure):
                 ("nops", ctypes.c_int),
                 ("njamp_updates", ctypes.c_int), ("denom", ctypes.c_int64),
                 ("iden", ctypes.c_double), ("flops_diagram", ctypes.c_double),
-                ("flops_colour", ctypes.c_double)]
+                ("flops_colour", ctypes.c_double), ("nchannel", ctypes.c_int)]
 
 
 class mg_sigmakin_extras(ctypes.Structure):
     _fields_ = [("alphas_dev", ctypes.c_void_p), ("channel", ctypes.c_int),
                 ("sde_weight_dev", ctypes.c_void_p), ("flow_weight_dev", ctypes.c_void_p),
                 ("rnd_hel_dev", ctypes.c_void_p), ("hel_out_dev", ctypes.c_void_p),
-                ("rnd_col_dev", ctypes.c_void_p), ("col_out_dev", ctypes.c_void_p)]
+                ("rnd_col_dev", ctypes.c_void_p), ("col_out_dev", ctypes.c_void_p),
+                ("channel_ids_dev", ctypes.c_void_p)]
 
 
 class MGError(RuntimeError):
@@ -69,6 +70,7 @@ _SIGS = {
     "mg_process_info": ([_VP, ctypes.POINTER(mg_info)], ctypes.c_int),
     "mg_color_matrix": ([_VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "mg_helicity_mask": ([_VP, ctypes.POINTER(ctypes.c_uint8)], ctypes.c_int),
+    "mg_sde_channels": ([_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int8)], ctypes.c_int),
     "mg_process_destroy": ([_VP], None),
     "mg_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "mg_last_cuda_error": ([], ctypes.c_char_p),
@@ -198,9 +200,10 @@ class Process:
         return {k: (ms[i], n[i]) for i, k in enumerate(("diagram", "colour", "event_sum"))}
 
     def sigmakin_ex(self, momenta, out=None, alphas=None, channel=-1, sde=None, flow=None,
-                    rnd_hel=None, hel_out=None, rnd_col=None, col_out=None, stream=None):
+                    rnd_hel=None, hel_out=None, rnd_col=None, col_out=None, channel_ids=None,
+                    stream=None):
         x = mg_sigmakin_extras(_ptr(alphas), channel, _ptr(sde), _ptr(flow), _ptr(rnd_hel),
-                               _ptr(hel_out), _ptr(rnd_col), _ptr(col_out))
+                               _ptr(hel_out), _ptr(rnd_col), _ptr(col_out), _ptr(channel_ids))
         _check(lib().mg_sigmakin_ex(self._h, _ptr(momenta), momenta.shape[0], ctypes.byref(x),
                                     _ptr(out), _stream(stream)), "mg_sigmakin_ex")
         return out
@@ -216,6 +219,16 @@ class Process:
         _check(lib().mg_color_matrix(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                                      ctypes.byref(d)), "mg_color_matrix")
         return a.reshape(nc, nc), d.value
+
+    def sde_channels(self):
+        """Colour-factor codes [nchannel][ncolor] (int8) of the channels."""
+        import numpy as np
+        n = ctypes.c_int(0)
+        _check(lib().mg_sde_channels(self._h, ctypes.byref(n), None), "mg_sde_channels")
+        codes = np.zeros((n.value, self.info().ncolor), dtype=np.int8)
+        _check(lib().mg_sde_channels(self._h, None, codes.ctypes.data_as(ctypes.POINTER(ctypes.c_int8))),
+               "mg_sde_channels")
+        return codes
 
     def helicity_mask(self):
         import numpy as np

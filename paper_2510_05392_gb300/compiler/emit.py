@@ -4,6 +4,9 @@ For every supported process the generated include file holds:
   OPS    int32[nops][8]   the wavefunction/amplitude program (program.py)
   SCAT   int32[nscat]     jamp scatter entries (flow * 4 + coefficient code)
   CHAT   int32[nc][nc]    integer colour matrix D * C (colour.py)
+  CHO    int32[nch + 1]   single-diagram-enhancement channels: offsets into CHF
+  CHF    int32[...]       per channel its colour factor, flow * 8 + code
+                          (program.py: 1 +1, 2 -1, 3 +i, 4 -i; first entry +1)
 and one registry row with the sizes, the common denominator D, the averaging
 factor and the algorithmic FP64 operation counts per helicity.
 
@@ -80,6 +83,16 @@ def algorithmic_flops(prog: program.Program) -> dict:
     return dict(diagram=unit / 4.0, colour=csum)
 
 
+def channel_tables(prog: program.Program):
+    """(offsets [nchannel + 1], entries flow * 8 + code) of the channels'
+    colour factors."""
+    off, ent = [0], []
+    for ch in prog.channels:
+        ent.extend(f * 8 + c for f, c in ch)
+        off.append(len(ent))
+    return off, ent
+
+
 def _arr(name, vals, per_line=16):
     out = [f"static const int32_t {name}[{max(1, len(vals))}] = {{"]
     for i in range(0, len(vals), per_line):
@@ -111,6 +124,9 @@ def emit(path: str, max_gluons: int = 6, list_path: str | None = None) -> None:
         lines.append(_arr(f"OPS_{name}", flat_ops))
         lines.append(_arr(f"SCAT_{name}", prog.scatter))
         lines.append(_arr(f"CHAT_{name}", flat_c))
+        cho, chf = channel_tables(prog)
+        lines.append(_arr(f"CHO_{name}", cho))
+        lines.append(_arr(f"CHF_{name}", chf))
         fl = algorithmic_flops(prog)
         iden = 256 * math.factorial(n - 2)
         rows.append(
@@ -118,7 +134,7 @@ def emit(path: str, max_gluons: int = 6, list_path: str | None = None) -> None:
             f'{prog.ncolor}, {prog.nslot}, {prog.nslot_f}, {prog.nslot_acc}, {len(prog.ops)}, '
             f'{len(prog.scatter)}, '
             f'{D}LL, {iden}.0, {fl["diagram"]!r}, {fl["colour"]}.0, OPS_{name}, SCAT_{name}, '
-            f'CHAT_{name}}},')
+            f'CHAT_{name}, NULL, NULL, {len(prog.channels)}, CHO_{name}, CHF_{name}}},')
         xlist.append(f"X({len(rows) - 1}, {n}, {prog.nslot}, {prog.nslot_f}, {max(1, prog.nslot_acc)}, "
                      f"{prog.ncolor})")
         lines.append("")
@@ -136,14 +152,15 @@ def emit(path: str, max_gluons: int = 6, list_path: str | None = None) -> None:
 
 
 # Binary process table (little-endian), read by mg_process_create_from_tables:
-#   char[8]  "MGPROC01"
-#   int32[12] version (1), ngluon, npar, ncolor, nops, nscat, nslot (gluon),
-#             nslot_top, nslot_acc, ncolour_groups, ndiagrams, nterms
+#   char[8]  "MGPROC02"
+#   int32[13] version (2), ngluon, npar, ncolor, nops, nscat, nslot (gluon),
+#             nslot_top, nslot_acc, ncolour_groups, ndiagrams, nterms, nchannel
 #   int64    D (common denominator);  float64 iden, flops_diagram, flops_colour
 #   int32    ops[nops][8];  int32 scat[nscat]
 #   int64    row[ncolor]    D * C_(id, r) by relative ordering r (colour.relative_row)
 #   int8     perms[ncolor][ngluon]   the flow orderings, itertools order
-BLOB_MAGIC = b"MGPROC01"
+#   int32    chan_off[nchannel + 1];  int32 chan_flows[chan_off[nchannel]]
+BLOB_MAGIC = b"MGPROC02"
 
 
 def emit_blob(n: int, path: str) -> None:
@@ -153,14 +170,17 @@ def emit_blob(n: int, path: str) -> None:
     iden = 256 * math.factorial(n - 2)
     with open(path + ".tmp", "wb") as f:
         f.write(BLOB_MAGIC)
-        f.write(struct.pack("<12i", 1, n, n + 2, prog.ncolor, len(prog.ops), len(prog.scatter),
+        f.write(struct.pack("<13i", 2, n, n + 2, prog.ncolor, len(prog.ops), len(prog.scatter),
                             prog.nslot, prog.nslot_f, max(1, prog.nslot_acc), prog.ncolour_groups,
-                            prog.ndiagrams, prog.nterms))
+                            prog.ndiagrams, prog.nterms, len(prog.channels)))
         f.write(struct.pack("<q3d", D, float(iden), float(fl["diagram"]), float(fl["colour"])))
         f.write(struct.pack(f"<{8 * len(prog.ops)}i", *[v for r in prog.ops for v in r]))
         f.write(struct.pack(f"<{len(prog.scatter)}i", *prog.scatter))
         f.write(struct.pack(f"<{len(row)}q", *row))
         f.write(bytes(v for p in prog.perms for v in p))
+        cho, chf = channel_tables(prog)
+        f.write(struct.pack(f"<{len(cho)}i", *cho))
+        f.write(struct.pack(f"<{len(chf)}i", *chf))
     import os
     os.replace(path + ".tmp", path)
 

@@ -46,6 +46,8 @@ OPNAMES = {v: k for k, v in dict(globals()).items() if k.startswith("OP_")}
 
 # jamp coefficient codes: amp * {+1, -1, +i, -i}
 COEF_CODE = {1: 0, -1: 1, 1j: 2, -1j: 3}
+# channel colour-factor codes (0: flow absent)
+CHANNEL_CODE = {1: 1, -1: 2, 1j: 3, -1j: 4}
 
 # FP64 instruction counts per op (FMA = 1), used for the algorithmic flop
 # count: see flops_per_op(); kept next to the opcode table.
@@ -62,6 +64,7 @@ class Program:
     nslot_f: int = 0                               # top-line slots (2 variants)
     nslot_acc: int = 0                             # amplitude accumulators (4 variants)
     ncolour_groups: int = 0                        # distinct colour factors up to a phase
+    channels: list = field(default_factory=list)   # per channel: [(flow, code)] sorted by flow
     ndiagrams: int = 0
     nterms: int = 0
     perms: list = field(default_factory=list)      # colour-flow orderings
@@ -188,6 +191,11 @@ class _Builder:
         return self.obj[key]
 
 
+def _has_v4(c) -> bool:
+    """True when a gluon sub-tree contains a four-gluon vertex."""
+    return c.kind == "v4" or any(_has_v4(a) for a in c.args)
+
+
 def _mask(s) -> int:
     m = 0
     for g in s:
@@ -242,9 +250,9 @@ def build_program(n: int, order: str = "middle") -> Program:
 
     # Diagram terms whose colour factors agree up to a unit phase share their
     # scatter: their amplitudes are summed (with that phase) into an
-    # accumulator and the group's last member scatters the sum once.  (The
-    # number of such classes is the paper's count of single-diagram-enhancement
-    # channels: 3 / 15 / 105 / 945 for 2 to 5 gluons.)
+    # accumulator and the group's last member scatters the sum once.  (Each
+    # group holds exactly one diagram made of three-point vertices, so there
+    # are as many groups as single-diagram-enhancement channels below.)
     group_of, phase_of, rep = {}, {}, {}
     sorted_colour = {}     # a term's colour decomposition in flow order (used twice)
     for d, _ in terms:
@@ -259,6 +267,29 @@ def build_program(n: int, order: str = "middle") -> Program:
     members = {}
     for d, _ in terms:
         members.setdefault(group_of[d.idx], []).append(d.idx)
+
+    # Single-diagram-enhancement channels: the diagrams made of three-point
+    # vertices only (the paper's channel counts 3 / 15 / 105 / 945, the
+    # diagrams MadEvent's single diagram enhancement uses).  A channel is
+    # identified by its colour factor: the flow coefficients divided by the
+    # first one (flow order), coded 1: +1, 2: -1, 3: +i, 4: -i; channels are
+    # numbered in the lexicographic order of these code vectors over all
+    # flows (a zero entry, i.e. an absent flow, sorts lowest).  Terms with a
+    # four-gluon vertex belong to no channel (-1).
+    chan_code = {}
+    for d, _ in terms:
+        if any(_has_v4(b) for b in d.blocks):
+            continue
+        items = sorted_colour[d.idx]
+        c0 = complex(items[0][1])
+        chan_code[d.idx] = tuple((pidx[st], CHANNEL_CODE[complex(c) / c0]) for st, c in items)
+    # lexicographic order of the dense code vectors, from the sparse lists:
+    # at the first flow where two vectors differ the one with a coefficient
+    # there (rather than none) or with the larger code is larger
+    order = sorted(chan_code, key=lambda i: tuple((-f, c) for f, c in chan_code[i]))
+    channel_of = {i: k for k, i in enumerate(order)}
+    if len({chan_code[i] for i in order}) != len(order):
+        raise AssertionError("two channels share a colour factor")
     rep_items = {g: (it, c0) for _, (g, it, c0) in rep.items()}
 
     scatter = []
@@ -283,7 +314,7 @@ def build_program(n: int, order: str = "middle") -> Program:
             off = len(scatter)
             for string, c in sorted_colour[d.idx]:
                 scatter.append(pidx[string] * 4 + COEF_CODE[complex(c)])
-            B._emit(code, [], ins, [off, len(scatter) - off, None, 0, g])
+            B._emit(code, [], ins, [off, len(scatter) - off, None, 0, channel_of.get(d.idx, -1)])
             continue
         first, last = mem[0] == d.idx, mem[-1] == d.idx
         acc_key = ("ACC", g)
@@ -297,7 +328,7 @@ def build_program(n: int, order: str = "middle") -> Program:
                 scatter.append(pidx[string] * 4 + COEF_CODE[complex(c) / c0])
             cnt = len(scatter) - off
         mode = COEF_CODE[phase_of[d.idx]] | (4 if first else 0) | (8 if last else 0)
-        B._emit(code, outs, ins + acc_in, [off, cnt, "acc", mode, g])
+        B._emit(code, outs, ins + acc_in, [off, cnt, "acc", mode, channel_of.get(d.idx, -1)])
 
     # ------------------------------------------------ slot allocation ----
     # Three pools, by how many top-helicity variants an object carries:
@@ -356,7 +387,8 @@ def build_program(n: int, order: str = "middle") -> Program:
     prog = Program(n=n, npar=n + 2, ncolor=len(perms), ops=records, scatter=scatter,
                    nslot=nslot["G"], nslot_f=nslot["F"], nslot_acc=nslot["A"],
                    ndiagrams=P.ndiagrams, nterms=len(P.diagrams), perms=perms,
-                   ncolour_groups=len(rep))
+                   ncolour_groups=len(rep),
+                   channels=[list(chan_code[i]) for i in order])
     return prog
 
 
@@ -378,8 +410,9 @@ def _record(code, outs, ins, extra):
     elif code in (OP_XROW, OP_YCOL, OP_BIL):
         r[1], r[2], r[3] = outs[0], ins[0], ins[1]
     elif code in (OP_AMP_SS, OP_AMP_VV):
-        # [code, class, X, V, scatter offset, scatter count, accumulator (-1: none), mode]
-        # class: the colour-factor class (= single-diagram-enhancement channel)
+        # [code, channel, X, V, scatter offset, scatter count, accumulator (-1: none), mode]
+        # channel: the single-diagram-enhancement channel of a diagram made of
+        # three-point vertices only, -1 for a term with a four-gluon vertex
         # mode: bits 0-1 phase code of this amplitude in its group's sum, bit 2
         # first member (initialises the accumulator), bit 3 last member (scatters)
         r[1] = extra[4]

@@ -49,11 +49,11 @@ std::string normalise(const char *s) {
     return out;
 }
 
-// A device pointer usable by this process: non-null, 8-byte aligned, device
-// (or managed) memory of the process's device.
-int check_dev_ptr(const void *ptr, int device) {
+// A device pointer usable by this process: non-null, aligned (8 bytes unless
+// stated), device (or managed) memory of the process's device.
+int check_dev_ptr(const void *ptr, int device, int align = 8) {
     if (!ptr) return MG_ERR_BAD_ARG;
-    if (reinterpret_cast<uintptr_t>(ptr) % 8) return MG_ERR_BAD_ARG;
+    if (reinterpret_cast<uintptr_t>(ptr) % align) return MG_ERR_BAD_ARG;
     cudaPointerAttributes at;
     cudaError_t e = cudaPointerGetAttributes(&at, ptr);
     if (e != cudaSuccess) {
@@ -100,11 +100,14 @@ void free_proc(mg_process *p) {
     cudaFree(p->d_scratch);
     cudaFree(p->d_jrow);
     cudaFree(p->d_qpart);
+    cudaFree(p->d_sde_item);
     if (p->own_tab) {
         free((void *)p->own_tab->ops);
         free((void *)p->own_tab->scat);
         free((void *)p->own_tab->crow);
         free((void *)p->own_tab->cperm);
+        free((void *)p->own_tab->chan_off);
+        free((void *)p->own_tab->chan_flows);
         free(p->own_tab);
     }
     free(p);
@@ -181,11 +184,12 @@ int setup_mixed(mg_process *p) {
 // the colour-sum kernel forms every row's quadratic form per 64-colour tile
 // and the event sum adds them up.
 // Per-event extras of a table-file process (mg_sigmakin_ex): alphas [nevt]
-// or NULL, channel and sde [nevt] (channel >= 0), flow weights jw
-// [nevt][ncolor] or NULL.
+// or NULL, channel (or per-event channel_ids) and sde [nevt] (NULL: no
+// weights), flow weights jw [nevt][ncolor] or NULL.
 struct BigExtras {
     const double *alphas;
     int channel;
+    const int *channel_ids;
     double *sde;
     double *jw;
 };
@@ -253,12 +257,16 @@ int sigmakin_big(mg_process *p, const double *mom, int64_t nevt, double *me, dou
         if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? MG_ERR_NO_MEMORY : cuda_fail(e);
         p->jrow_items = nipad_max;
     }
-    double *sde_item = nullptr;   // per-item channel sums, one chunk
-    const bool want_sde = bx && bx->channel >= 0;
-    if (want_sde) {
-        cudaError_t e = cudaMalloc(&sde_item, sizeof(double) * 8 * nipad_max);
+    const bool want_sde = bx && bx->sde;
+    if (want_sde && nipad_max > p->sde_item_cap) {   // per-item channel sums, one chunk
+        cudaFree(p->d_sde_item);
+        p->d_sde_item = nullptr;
+        p->sde_item_cap = 0;
+        cudaError_t e = cudaMalloc(&p->d_sde_item, sizeof(double) * 8 * nipad_max);
         if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? MG_ERR_NO_MEMORY : cuda_fail(e);
+        p->sde_item_cap = nipad_max;
     }
+    double *sde_item = want_sde ? p->d_sde_item : nullptr;
     int rc = MG_OK;
     const mg_dev_proc dp = dev_view(p);
     for (long long e0 = 0; e0 < nevt; e0 += ev_chunk) {
@@ -271,7 +279,9 @@ int sigmakin_big(mg_process *p, const double *mom, int64_t nevt, double *me, dou
         if (e == cudaSuccess)
             e = mg_launch_sigmakin_big(dp, mom + e0 * t->npar * 4, nitem, p->d_units, nu, t->nslot,
                                        t->nslot_top, p->d_scratch, T, p->d_jrow, R, nip, s,
-                                       want_sde ? bx->channel : -1, sde_item);
+                                       want_sde ? bx->channel : -1,
+                                       want_sde && bx->channel_ids ? bx->channel_ids + e0 : nullptr,
+                                       sde_item);
         mg_timer_end(p, s, slot);
         slot = mg_timer_begin(p, s, MG_KT_COLOUR);
         if (e == cudaSuccess && mixed) {
@@ -297,11 +307,6 @@ int sigmakin_big(mg_process *p, const double *mom, int64_t nevt, double *me, dou
             rc = cuda_fail(e);
             break;
         }
-    }
-    if (sde_item) {   // the chunk kernels read it: release after they ran
-        cudaError_t e = cudaStreamSynchronize(s);
-        cudaFree(sde_item);
-        if (rc == MG_OK && e != cudaSuccess) rc = cuda_fail(e);
     }
     return rc;
 }
@@ -333,7 +338,8 @@ bool valid_program(const mg_proc_table *t) {
             case MG_OP_AMP_SS:
             case MG_OP_AMP_VV:
                 ok = (c == MG_OP_AMP_SS ? in(az, nsf) && in(aw, nsf) : in(aw, nsg)) && bx >= 0 &&
-                     by >= 0 && (long long)bx + by <= t->nscat && (bz == -1 || in(bz, nsa));
+                     by >= 0 && (long long)bx + by <= t->nscat && (bz == -1 || in(bz, nsa)) &&
+                     (ay == -1 || in(ay, t->nchannel));
                 break;
             default: ok = false;
         }
@@ -341,6 +347,14 @@ bool valid_program(const mg_proc_table *t) {
     }
     for (int i = 0; i < t->nscat; i++)
         if (t->scat[i] < 0 || (t->scat[i] >> 2) >= t->ncolor) return false;
+    if (t->chan_off[0] != 0) return false;
+    for (int c = 0; c < t->nchannel; c++) {
+        if (t->chan_off[c + 1] <= t->chan_off[c]) return false;
+        for (int i = t->chan_off[c]; i < t->chan_off[c + 1]; i++) {
+            const int f = t->chan_flows[i];
+            if (f < 0 || (f >> 3) >= t->ncolor || (f & 7) < 1 || (f & 7) > 4) return false;
+        }
+    }
     for (int a = 0; a < t->ncolor; a++) {
         unsigned seen = 0;
         for (int q = 0; q < ng; q++) {
@@ -357,16 +371,16 @@ mg_proc_table *read_table_file(const char *path, int *status) {
     FILE *f = fopen(path, "rb");
     if (!f) return nullptr;
     char magic[8];
-    int32_t h[12];
+    int32_t h[13];
     int64_t den;
     double dv[3];
     mg_proc_table *t = (mg_proc_table *)calloc(1, sizeof(mg_proc_table));
-    bool ok = t && fread(magic, 1, 8, f) == 8 && memcmp(magic, "MGPROC01", 8) == 0 &&
-              fread(h, sizeof(int32_t), 12, f) == 12 && fread(&den, 8, 1, f) == 1 &&
+    bool ok = t && fread(magic, 1, 8, f) == 8 && memcmp(magic, "MGPROC02", 8) == 0 &&
+              fread(h, sizeof(int32_t), 13, f) == 13 && fread(&den, 8, 1, f) == 1 &&
               fread(dv, 8, 3, f) == 3;
     if (ok) {
-        ok = h[0] == 1 && h[1] == mg_big_ngluon() && h[2] == h[1] + 2 && h[3] > 0 && h[4] > 0 &&
-             h[5] >= 0 && h[6] > 0 && h[7] > 0 && h[8] > 0 && den > 0;
+        ok = h[0] == 2 && h[1] == mg_big_ngluon() && h[2] == h[1] + 2 && h[3] > 0 && h[4] > 0 &&
+             h[5] >= 0 && h[6] > 0 && h[7] > 0 && h[8] > 0 && h[12] > 0 && den > 0;
         long long fact = 1;
         for (int i = 2; i <= h[1]; i++) fact *= i;
         ok = ok && h[3] == fact;
@@ -382,6 +396,7 @@ mg_proc_table *read_table_file(const char *path, int *status) {
         t->nslot_acc = h[8];
         t->ndiagrams = h[10];
         t->nterms = h[11];
+        t->nchannel = h[12];
         t->denom = den;
         t->iden = dv[0];
         t->flops_diagram = dv[1];
@@ -390,16 +405,26 @@ mg_proc_table *read_table_file(const char *path, int *status) {
         int32_t *scat = (int32_t *)malloc(sizeof(int32_t) * (t->nscat > 0 ? t->nscat : 1));
         int64_t *row = (int64_t *)malloc(sizeof(int64_t) * t->ncolor);
         int8_t *perm = (int8_t *)malloc((size_t)t->ncolor * t->ngluon);
+        int32_t *choff = (int32_t *)malloc(sizeof(int32_t) * ((size_t)t->nchannel + 1));
         t->ops = ops;
         t->scat = scat;
         t->crow = row;
         t->cperm = perm;
-        ok = ops && scat && row && perm &&
+        t->chan_off = choff;
+        ok = ops && scat && row && perm && choff &&
              fread(ops, sizeof(int32_t), 8 * (size_t)t->nops, f) == 8 * (size_t)t->nops &&
              fread(scat, sizeof(int32_t), t->nscat, f) == (size_t)t->nscat &&
              fread(row, sizeof(int64_t), t->ncolor, f) == (size_t)t->ncolor &&
              fread(perm, 1, (size_t)t->ncolor * t->ngluon, f) == (size_t)t->ncolor * t->ngluon &&
-             fgetc(f) == EOF && valid_program(t);
+             fread(choff, sizeof(int32_t), (size_t)t->nchannel + 1, f) == (size_t)t->nchannel + 1;
+        // each channel has at most 2^(ngluon - 1) flows (one per planar ordering)
+        ok = ok && choff[t->nchannel] > 0 && choff[t->nchannel] <= t->nchannel * (1 << (t->ngluon - 1));
+        if (ok) {
+            int32_t *chf = (int32_t *)malloc(sizeof(int32_t) * (size_t)choff[t->nchannel]);
+            t->chan_flows = chf;
+            ok = chf && fread(chf, sizeof(int32_t), choff[t->nchannel], f) == (size_t)choff[t->nchannel] &&
+                 fgetc(f) == EOF && valid_program(t);
+        }
     }
     fclose(f);
     if (!ok) {
@@ -408,6 +433,8 @@ mg_proc_table *read_table_file(const char *path, int *status) {
             free((void *)t->scat);
             free((void *)t->crow);
             free((void *)t->cperm);
+            free((void *)t->chan_off);
+            free((void *)t->chan_flows);
             free(t);
         }
         return nullptr;
@@ -651,6 +678,20 @@ int mg_process_info(const mg_process *p, mg_info *o) {
     o->iden = t->iden;
     o->flops_diagram = t->flops_diagram;
     o->flops_colour = t->flops_colour;
+    o->nchannel = t->nchannel;
+    return MG_OK;
+}
+
+int mg_sde_channels(const mg_process *p, int *nchannel_out, int8_t *codes_out) {
+    if (!p || (!nchannel_out && !codes_out)) return MG_ERR_BAD_ARG;
+    const mg_proc_table *t = p->tab;
+    if (nchannel_out) *nchannel_out = t->nchannel;
+    if (codes_out) {
+        memset(codes_out, 0, (size_t)t->nchannel * t->ncolor);
+        for (int c = 0; c < t->nchannel; c++)
+            for (int i = t->chan_off[c]; i < t->chan_off[c + 1]; i++)
+                codes_out[(size_t)c * t->ncolor + (t->chan_flows[i] >> 3)] = (int8_t)(t->chan_flows[i] & 7);
+    }
     return MG_OK;
 }
 
@@ -1096,12 +1137,14 @@ extern "C" int mg_sigmakin_ex(mg_process *p, const double *mom, int64_t nevt,
     if (!st && x->alphas_dev) st = check_dev_ptr(x->alphas_dev, p->device);
     if (!st && x->sde_weight_dev) st = check_dev_ptr(x->sde_weight_dev, p->device);
     if (!st && x->flow_weight_dev) st = check_dev_ptr(x->flow_weight_dev, p->device);
+    if (!st && x->channel_ids_dev) st = check_dev_ptr(x->channel_ids_dev, p->device, 4);
     if (st) return st;
     const bool want_hel = x->hel_out_dev && x->rnd_hel_dev;
     const bool want_col = x->col_out_dev && x->rnd_col_dev;
     if ((x->hel_out_dev && !x->rnd_hel_dev) || (x->col_out_dev && !x->rnd_col_dev)) return MG_ERR_BAD_ARG;
-    if (x->channel >= 0 && !x->sde_weight_dev) return MG_ERR_BAD_ARG;
-    if (x->channel < -1) return MG_ERR_BAD_ARG;
+    const bool want_sde = x->channel >= 0 || x->channel_ids_dev;
+    if (want_sde && !x->sde_weight_dev) return MG_ERR_BAD_ARG;
+    if (x->channel < -1 || x->channel >= p->tab->nchannel) return MG_ERR_BAD_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const int nhel = 1 << p->tab->npar, nc = p->tab->ncolor;
     if ((want_hel || (want_col && !x->flow_weight_dev)) && nevt > p->sel_cap) {
@@ -1119,8 +1162,9 @@ extern "C" int mg_sigmakin_ex(mg_process *p, const double *mom, int64_t nevt,
     double *jw = x->flow_weight_dev ? x->flow_weight_dev : (want_col ? p->d_sel_jw : nullptr);
     if (mh) MG_CUDA(cudaMemsetAsync(mh, 0, sizeof(double) * nevt * nhel, s));
     if (p->big) {   // table-file process: extras from the chunked HBM pipeline
-        const BigExtras bx = {x->alphas_dev, x->channel, x->channel >= 0 ? x->sde_weight_dev : nullptr, jw};
-        if (!me && !mh && !jw && x->channel < 0) return MG_OK;
+        const BigExtras bx = {x->alphas_dev, x->channel, x->channel_ids_dev,
+                              want_sde ? x->sde_weight_dev : nullptr, jw};
+        if (!me && !mh && !jw && !want_sde) return MG_OK;
         st = sigmakin_big(p, mom, nevt, me, mh, s, &bx);
         if (st) return st;
         if (want_hel || want_col)
@@ -1133,7 +1177,8 @@ extern "C" int mg_sigmakin_ex(mg_process *p, const double *mom, int64_t nevt,
     ex.alphas = x->alphas_dev;
     ex.alphas0 = p->par.alphas;
     ex.channel = x->channel;
-    ex.sde = x->channel >= 0 ? x->sde_weight_dev : nullptr;
+    ex.channel_ids = x->channel_ids_dev;
+    ex.sde = want_sde ? x->sde_weight_dev : nullptr;
     ex.jw = jw;
     int tpe = p->tpe;
     while (tpe > 1 && tpe > p->nunits) tpe >>= 1;

@@ -121,8 +121,9 @@ __device__ __forceinline__ void prefetch_inputs(const int4 &a, const int4 &b, co
 // F (slot s, variant v, component m: 8 s + 4 v + m), A (slot s, variant v:
 // 4 s + v); jamp (c, v) of the item at jr[c * R / 2 + v * nipad] (real,
 // imaginary).
-// sde8 (may be NULL): per top-helicity combination v, |A_channel|^2 in [v]
-// and the sum over colour-factor classes of |A_class|^2 in [4 + v].
+// sde8 (may be NULL): per top-helicity combination v, |D_channel|^2 in [v]
+// and the sum over the single-diagram-enhancement channels (the diagram
+// terms of three-point vertices only) of |D|^2 in [4 + v].
 template <int NG>
 __device__ void run_item(const Kin<NG> &k, int g, const int4 *__restrict__ ops, int nops,
                          const int *__restrict__ scat, double mt, const Strided &WG,
@@ -242,6 +243,13 @@ __device__ void run_item(const Kin<NG> &k, int g, const int4 *__restrict__ ops, 
                     WG.ld4(4LL * a.w, w);
                     for (int v = 0; v < 4; v++) amp[v] = mdot(G0[v], w);
                 }
+                if (sde8 && a.y >= 0) {  // a diagram of three-point vertices: a channel
+                    for (int v = 0; v < 4; v++) {
+                        const double w = fma(amp[v].r, amp[v].r, amp[v].i * amp[v].i);
+                        sde8[4 + v] += w;
+                        if (a.y == channel) sde8[v] += w;
+                    }
+                }
                 if (b.z >= 0) {  // member of a colour-factor group
                     const int mode = b.w;
                     for (int v = 0; v < 4; v++) {
@@ -251,13 +259,6 @@ __device__ void run_item(const Kin<NG> &k, int g, const int4 *__restrict__ ops, 
                     if (!(mode & 8)) {
                         for (int v = 0; v < 4; v++) ACC.st(4LL * b.z + v, amp[v]);
                         break;
-                    }
-                }
-                if (sde8) {  // channel weight: |A_class|^2 over all classes and the chosen one
-                    for (int v = 0; v < 4; v++) {
-                        const double w = fma(amp[v].r, amp[v].r, amp[v].i * amp[v].i);
-                        sde8[4 + v] += w;
-                        if (a.y == channel) sde8[v] += w;
                     }
                 }
                 // jamp updates in batches: every old value of a batch is
@@ -301,7 +302,8 @@ __global__ void __launch_bounds__(BIG_BLOCK, 3)   // 168 registers: three blocks
                    const int *__restrict__ units, const int4 *__restrict__ ops, int nops,
                    const int *__restrict__ scat, double mt, double wt, double2 *__restrict__ scratch,
                    long long T, int nsg, int nsf, double *__restrict__ jrow, long long R,
-                   long long nipad, int channel, double *__restrict__ sde_item) {
+                   long long nipad, int channel, const int *__restrict__ channel_ids,
+                   double *__restrict__ sde_item) {
     constexpr int NPAR = NG + 2;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T) return;
@@ -315,8 +317,8 @@ __global__ void __launch_bounds__(BIG_BLOCK, 3)   // 168 registers: three blocks
         kinematics<NG>(k, mom + e * (NPAR * 4), mt, wt);
         double sde8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         run_item<NG>(k, u >> 4, ops, nops, scat, mt, WG, WF, ACC,
-                     reinterpret_cast<double2 *>(jrow) + item, R, nipad, channel,
-                     sde_item ? sde8 : nullptr);
+                     reinterpret_cast<double2 *>(jrow) + item, R, nipad,
+                     channel_ids ? __ldg(channel_ids + e) : channel, sde_item ? sde8 : nullptr);
         if (sde_item)
             for (int q = 0; q < 8; q++) sde_item[item * 8 + q] = sde8[q];
     }
@@ -573,13 +575,14 @@ cudaError_t mg_launch_rows_to_bf16(const double *jrow, long long R, int nsrc, in
 cudaError_t mg_launch_sigmakin_big(const mg_dev_proc &dp, const double *mom, long long nitem,
                                    const int *units, int nunits, int nsg, int nsf, double2 *scratch,
                                    long long T, double *jrow, long long R, long long nipad,
-                                   cudaStream_t stream, int channel, double *sde_item) {
+                                   cudaStream_t stream, int channel, const int *channel_ids,
+                                   double *sde_item) {
     if (nitem <= 0) return cudaSuccess;
     if (T <= 0 || T % BIG_BLOCK || R != 8 * nipad || nipad < nitem) return cudaErrorInvalidValue;
     mg_note_launch();
     k_sigmakin_big<BIG_NG><<<(unsigned)(T / BIG_BLOCK), BIG_BLOCK, 0, stream>>>(
         mom, nitem, nunits, units, reinterpret_cast<const int4 *>(dp.ops), dp.nops, dp.scat, dp.mt,
-        dp.wt, scratch, T, nsg, nsf, jrow, R, nipad, channel, sde_item);
+        dp.wt, scratch, T, nsg, nsf, jrow, R, nipad, channel, channel_ids, sde_item);
     return cudaGetLastError();
 }
 

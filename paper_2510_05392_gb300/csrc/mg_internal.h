@@ -27,6 +27,9 @@ typedef struct {
     const int32_t *chat;     // [ncolor][ncolor], D * C (NULL for table-file processes)
     const int64_t *crow;     // table-file processes: D * C by relative ordering [ncolor]
     const int8_t *cperm;     // table-file processes: flow orderings [ncolor][ngluon]
+    int nchannel;            // single-diagram-enhancement channels
+    const int32_t *chan_off; // [nchannel + 1] offsets into chan_flows
+    const int32_t *chan_flows; // per channel its colour factor: flow * 8 + code
 } mg_proc_table;
 
 const mg_proc_table *mg_tables(int *count);
@@ -69,8 +72,9 @@ typedef struct {
 typedef struct {
     const double *alphas;  // per-event alpha_s [nevt] or NULL
     double alphas0;        // alpha_s the couplings were built with
-    int channel;           // single-diagram-enhancement channel (colour-factor class) or -1
-    double *sde;           // out [nevt]: |A_channel|^2 / sum_classes |A|^2 (channel >= 0)
+    int channel;           // single-diagram-enhancement channel of every event, or -1
+    const int *channel_ids;// per-event channels [nevt] (overrides channel) or NULL
+    double *sde;           // out [nevt]: |D_channel|^2 / sum_channels |D|^2, or NULL
     double *jw;            // out [nevt][ncolor]: helicity-summed |J_s|^2, or NULL
 } mg_extras;
 
@@ -128,7 +132,8 @@ cudaError_t mg_launch_build_cbig(const long long *row, const signed char *perm, 
 cudaError_t mg_launch_sigmakin_big(const mg_dev_proc &dp, const double *mom, long long nitem,
                                    const int *units, int nunits, int nsg, int nsf, double2 *scratch,
                                    long long T, double *jrow, long long R, long long nipad,
-                                   cudaStream_t stream, int channel = -1, double *sde_item = nullptr);
+                                   cudaStream_t stream, int channel = -1,
+                                   const int *channel_ids = nullptr, double *sde_item = nullptr);
 cudaError_t mg_launch_flow_weights_big(const double *jrow, long long R, long long nipad,
                                        const int *units, int nunits, long long nevt, int ncolor,
                                        double *jw, cudaStream_t stream);

@@ -36,7 +36,10 @@ namespace {
 // wavefunctions (pool WG) are computed once for the four; top-line objects
 // (pool WF) carry the two helicities of the top (ubar side) or of the antitop
 // (v side); the bilinear G0, the amplitudes and the jamps carry all four.
-// Writes me4[v] = sum_ij D*C_ij Re(J_v,i^* J_v,j).
+// Writes me4[v] = sum_ij D*C_ij Re(J_v,i^* J_v,j).  With sde8, adds per
+// variant v the |D|^2 of the single-diagram-enhancement channel `channel` to
+// sde8[v] and of every channel to sde8[4 + v] (a channel's amplitude is the
+// value of its one diagram term; its colour coefficients have modulus one).
 template <int NG, int NSG, int NSF, int NSA, int NC>
 __device__ void run_unit(const Kin<NG> &k, int g, const int4 *__restrict__ ops, int nops,
                          const int *__restrict__ scat, const double *__restrict__ cup, double mt,
@@ -113,6 +116,13 @@ __device__ void run_unit(const Kin<NG> &k, int g, const int4 *__restrict__ ops, 
                 } else {
                     for (int v = 0; v < 4; v++) amp[v] = mdot(G0[v], WG[a.w]);
                 }
+                if (sde8 && a.y >= 0) {  // a diagram of three-point vertices: a channel
+                    for (int v = 0; v < 4; v++) {
+                        const double w = fma(amp[v].r, amp[v].r, amp[v].i * amp[v].i);
+                        sde8[4 + v] += w;
+                        if (a.y == channel) sde8[v] += w;
+                    }
+                }
                 if (b.z >= 0) {  // member of a colour-factor group
                     const int mode = b.w;
                     if (mode & 4) {
@@ -122,13 +132,6 @@ __device__ void run_unit(const Kin<NG> &k, int g, const int4 *__restrict__ ops, 
                     }
                     if (!(mode & 8)) break;
                     for (int v = 0; v < 4; v++) amp[v] = ACC[b.z][v];
-                }
-                if (sde8) {  // channel weight: |A_class|^2 over all classes and the chosen one
-                    for (int v = 0; v < 4; v++) {
-                        const double w = fma(amp[v].r, amp[v].r, amp[v].i * amp[v].i);
-                        sde8[4 + v] += w;
-                        if (a.y == channel) sde8[v] += w;
-                    }
                 }
                 const int end = b.x + b.y;
                 for (int s = b.x; s < end; s++) {
@@ -226,6 +229,7 @@ __global__ void __launch_bounds__(EX ? 256 : 128, EX ? 1 : 3)
     double sum = 0.0;
     // per-event extras (compiled only into the EX instantiation)
     double sde8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const int channel = (EX && ex.channel_ids && e < nevt) ? __ldg(ex.channel_ids + e) : ex.channel;
     double num = 0.0, den = 0.0;
     double jw[EX ? NC : 1];
     if (EX && ex.jw)
@@ -251,7 +255,7 @@ __global__ void __launch_bounds__(EX ? 256 : 128, EX ? 1 : 3)
             if (EX)
                 for (int q = 0; q < 8; q++) sde8[q] = 0.0;
             run_unit<NG, NSG, NSF, NSA, NC>(k, g, ops, nops, scat, cup, mt, WG, WF, G0, ACC, J, me4,
-                                            !jout, ex.channel, (EX && ex.sde) ? sde8 : nullptr);
+                                            !jout, channel, (EX && ex.sde) ? sde8 : nullptr);
             if (jout) {
                 write_jamp_rows<NC>(J, mask, jout, (e * nunits_pad + iu) * 8, kp);
                 continue;
@@ -424,6 +428,7 @@ cudaError_t mg_launch_sigmakin(const mg_dev_proc &dp, const double *mom, int64_t
         ex.alphas = nullptr;
         ex.alphas0 = 1.0;
         ex.channel = -1;
+        ex.channel_ids = nullptr;
         ex.sde = nullptr;
         ex.jw = nullptr;
     }

@@ -53,6 +53,8 @@ struct mg_process {
     long long jrow_items;        // items (padded) the row buffer holds
     double *d_qpart;             // per-tile colour sums of one chunk
     long long qpart_len;
+    double *d_sde_item;          // per-item channel sums of one chunk (extras)
+    long long sde_item_cap;      // items it holds
 };
 
 // kinds of timed launches

@@ -52,3 +52,19 @@ def test_plain_c_program_against_the_headers(tmp_path):
     assert r.returncode == 0, r.stderr
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
+
+
+def test_library_exports_every_declared_function():
+    """Every function the public headers declare is exported by the built
+    library."""
+    import ctypes
+    import re
+    lib = ctypes.CDLL(build.build())
+    names = set()
+    for h in ("mgpu.h", "mgpu_bench.h", "mgpu_surrogate.h"):
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(mg_\w+)\s*\(", text))
+    assert len(names) > 30
+    missing = [n for n in sorted(names) if not hasattr(lib, n)]
+    assert not missing, missing

@@ -18,7 +18,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 GOLDEN = os.path.join(ROOT, "tests", "golden", "paper_table_complexity.json")
 
 
-@pytest.mark.parametrize("n", [2, 3, 4, 5])
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 6, 7])
 def test_diagram_counts_match_paper(n):
     g = json.load(open(GOLDEN))["processes"]
     proc = "g g > t t~" + " g" * (n - 2)
@@ -125,9 +125,32 @@ def test_null_arguments_rejected_without_gpu():
     assert L.mg_process_info(None, None) == binding.MG_ERR_BAD_ARG
 
 
-@pytest.mark.parametrize("n", [2, 3, 4, 5])
-def test_colour_factor_classes_equal_sde_channel_counts(n):
-    """Diagram terms whose colour factors agree up to a phase form as many
-    classes as the paper's table lists single-diagram-enhancement channels."""
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 6])
+def test_sde_channels_match_paper(n):
+    """The single-diagram-enhancement channels (diagrams of three-point
+    vertices only) are as many as the paper's table lists (2 to 5 gluons; it
+    gives none beyond), and as many as the trees with trivalent vertices,
+    (2n - 1)!!; the colour-factor groups of the program hold one channel each."""
     g = json.load(open(GOLDEN))["processes"]["g g > t t~" + " g" * (n - 2)]
-    assert program.build_program(n).ncolour_groups == g["sde_channels"]
+    prog = program.build_program(n)
+    if g["sde_channels"] is not None:
+        assert len(prog.channels) == g["sde_channels"]
+    assert len(prog.channels) == int(np.prod(np.arange(1, 2 * n, 2)))
+    assert prog.ncolour_groups == len(prog.channels)
+    amp = [op for op in prog.ops if op[0] in (program.OP_AMP_SS, program.OP_AMP_VV)]
+    used = sorted(op[1] for op in amp if op[1] >= 0)
+    assert used == list(range(len(prog.channels)))     # one diagram term per channel
+
+
+@pytest.mark.parametrize("n", [2, 3, 4])
+def test_sde_channels_match_oracle_diagrams(n):
+    """The compiler's channels are, code for code and in the same order, the
+    trivalent diagrams of the oracle's own diagram enumeration with colour
+    factors from explicit Gell-Mann matrices (oracle/sde.py)."""
+    from oracle import sde
+    prog = program.build_program(n)
+    dense = np.zeros((len(prog.channels), prog.ncolor), dtype=np.int8)
+    for c, ch in enumerate(prog.channels):
+        for f, code in ch:
+            dense[c, f] = code
+    assert np.array_equal(dense, sde.channels(n)[1])

@@ -55,19 +55,58 @@ def test_flow_weights_match_oracle_colour_ordered_amplitudes(ng):
         assert np.abs(got[e] - ref).max() <= 1e-9 * ref.max()
 
 
-def test_sde_weights_sum_to_one_over_channels():
-    p, mom, md = _setup(1, 17, 5300)
-    w = []
-    for c in range(15):
-        sde = torch.empty(17, dtype=torch.float64, device="cuda")
-        p.sigmakin_ex(md, None, channel=c, sde=sde)
-        w.append(sde)
+@pytest.mark.parametrize("ng", [0, 1, 2])
+def test_sde_channels_match_oracle(ng):
+    """The library's channels are the oracle's trivalent diagrams, colour
+    code for colour code and in the same order (3 / 15 / 105 channels)."""
+    from oracle import sde
+    p = binding.Process("g g > t t~" + " g" * ng)
+    codes = p.sde_channels()
+    assert p.info().nchannel == len(codes) == [3, 15, 105][ng]
+    assert np.array_equal(codes, sde.channels(ng + 2)[1])
+
+
+@pytest.mark.parametrize("ng", [0, 1, 2])
+def test_sde_weights_match_oracle_every_channel(ng):
+    """Single-diagram-enhancement weight of every channel for every event,
+    element by element against the oracle's diagram-by-diagram evaluation
+    (textbook Feynman rules, colour from Gell-Mann matrices), through
+    per-event channel ids: every (event, channel) pair in one call."""
+    from oracle import sde
+    n = 4
+    p, mom, _ = _setup(ng, n, 5300 + ng)
+    ref = sde.sde_weights(mom)                       # [n][nchannel]
+    nch = ref.shape[1]
+    rep = torch.from_numpy(np.repeat(mom, nch, axis=0)).cuda()
+    ids = torch.from_numpy(np.tile(np.arange(nch, dtype=np.int32), n)).cuda()
+    w = torch.empty(n * nch, dtype=torch.float64, device="cuda")
+    p.sigmakin_ex(rep, None, channel_ids=ids, sde=w)
+    # the whole-call channel gives the same numbers as the per-event ids
+    one = torch.empty(n, dtype=torch.float64, device="cuda")
+    p.sigmakin_ex(torch.from_numpy(mom).cuda(), None, channel=nch - 1, sde=one)
     torch.cuda.synchronize()
-    W = torch.stack(w).cpu().numpy()
-    assert np.all(W >= 0) and np.all(W <= 1)
-    np.testing.assert_allclose(W.sum(0), 1.0, rtol=1e-12)
+    got = w.cpu().numpy().reshape(n, nch)
+    err = np.abs(got - ref)
+    print(f"ng={ng}: max |dw| {err.max():.2e}, max rel {(err / np.maximum(ref, 1e-300)).max():.2e}")
+    assert (err <= 1e-9 * ref + 1e-15).all()
+    assert np.array_equal(one.cpu().numpy(), got[:, nch - 1])
+    np.testing.assert_allclose(got.sum(axis=1), 1.0, rtol=1e-12)
+
+
+def test_sde_argument_errors_and_out_of_range_ids():
+    p, mom, md = _setup(1, 4, 5350)
+    ids = torch.tensor([0, 15, -1, 14], dtype=torch.int32, device="cuda")
+    w = torch.empty(4, dtype=torch.float64, device="cuda")
+    p.sigmakin_ex(md, None, channel_ids=ids, sde=w)
+    torch.cuda.synchronize()
+    got = w.cpu().numpy()
+    assert got[1] == 0.0 and got[2] == 0.0 and got[0] > 0.0 and got[3] > 0.0
     with pytest.raises(binding.MGError):
-        p.sigmakin_ex(md, None, channel=0)   # weight output missing
+        p.sigmakin_ex(md, None, channel=0)           # weight output missing
+    with pytest.raises(binding.MGError):
+        p.sigmakin_ex(md, None, channel_ids=ids)     # weight output missing
+    with pytest.raises(binding.MGError):
+        p.sigmakin_ex(md, None, channel=15, sde=w)   # 15 channels: 0..14
 
 
 def test_helicity_and_colour_choice():

@@ -14,17 +14,20 @@ from paper_2510_05392_gb300 import binding
 BAD_PROCESS = -1
 
 
-def _blob(ops=None, scat=(), perms=None, magic=b"MGPROC01", version=1, ncolor=5040, trailing=b"",
-          nslot=(1, 1, 1)):
+def _blob(ops=None, scat=(), perms=None, magic=b"MGPROC02", version=2, ncolor=5040, trailing=b"",
+          nslot=(1, 1, 1), chan_off=(0, 1), chan_flows=(1,)):
     ops = ops if ops is not None else [[2, 0, 0, 0, 0, 0, 0, 0], [10, 0, 0, 0, 0, 0, 0, 0]]
     perms = perms if perms is not None else list(itertools.permutations(range(7)))
     out = magic
-    out += struct.pack("<12i", version, 7, 9, ncolor, len(ops), len(scat), *nslot, 1, 1, 1)
+    out += struct.pack("<13i", version, 7, 9, ncolor, len(ops), len(scat), *nslot, 1, 1, 1,
+                       len(chan_off) - 1)
     out += struct.pack("<q3d", 11664, 30720.0, 1.0, 1.0)
     out += struct.pack(f"<{8 * len(ops)}i", *[v for r in ops for v in r])
     out += struct.pack(f"<{len(scat)}i", *scat)
     out += struct.pack("<5040q", *([1] * 5040))
     out += bytes(v for p in perms for v in p)
+    out += struct.pack(f"<{len(chan_off)}i", *chan_off)
+    out += struct.pack(f"<{len(chan_flows)}i", *chan_flows)
     return out + trailing
 
 
@@ -47,15 +50,16 @@ def test_well_formed_file_passes_the_host_checks(tmp_path):
 
 @pytest.mark.parametrize("case", [
     "magic", "version", "ncolor", "truncated", "trailing", "slot_out_of_range",
-    "scatter_flow_out_of_range", "scatter_range_past_end", "not_a_permutation", "bad_opcode"])
+    "scatter_flow_out_of_range", "scatter_range_past_end", "not_a_permutation", "bad_opcode",
+    "channel_out_of_range", "channel_flow_out_of_range", "channel_code", "channel_offsets"])
 def test_damaged_file_is_rejected(tmp_path, case):
     perms = list(itertools.permutations(range(7)))
     amp = [11, 0, 0, 0, 0, 1, -1, 0]                      # AMP_SS scattering entry 0
     kw = {}
     if case == "magic":
-        kw["magic"] = b"MGPROC02"
+        kw["magic"] = b"MGPROC01"                         # the previous layout
     elif case == "version":
-        kw["version"] = 2
+        kw["version"] = 1
     elif case == "ncolor":
         kw["ncolor"] = 5039
     elif case == "trailing":
@@ -73,6 +77,16 @@ def test_damaged_file_is_rejected(tmp_path, case):
         kw["perms"] = perms
     elif case == "bad_opcode":
         kw["ops"] = [[13, 0, 0, 0, 0, 0, 0, 0]]
+    elif case == "channel_out_of_range":
+        kw["ops"] = [[2, 0, 0, 0, 0, 0, 0, 0], [11, 1, 0, 0, 0, 1, -1, 0]]   # channel 1 of 1
+        kw["scat"] = (0,)
+    elif case == "channel_flow_out_of_range":
+        kw["chan_flows"] = (5040 * 8 + 1,)
+    elif case == "channel_code":
+        kw["chan_flows"] = (5,)
+    elif case == "channel_offsets":
+        kw["chan_off"] = (0, 1, 1)
+        kw["chan_flows"] = (1,)
     data = _blob(**kw)
     if case == "truncated":
         data = data[:-100]
@@ -87,19 +101,19 @@ def test_missing_file(tmp_path):
 
 def test_emitter_round_trip(tmp_path):
     """The process compiler's table file holds exactly its program, scatter
-    list, colour row and flow orderings (written for g g > t t~ g g here; the
-    library itself only loads 7-gluon files)."""
+    list, colour row, flow orderings and channel colour factors (written for
+    g g > t t~ g g here; the library itself only loads 7-gluon files)."""
     from paper_2510_05392_gb300.compiler import colour, emit, program
     f = tmp_path / "g4.bin"
     emit.emit_blob(4, str(f))
     data = f.read_bytes()
-    assert data[:8] == b"MGPROC01"
-    h = struct.unpack_from("<12i", data, 8)
-    den, iden, fd, fc = struct.unpack_from("<q3d", data, 56)
+    assert data[:8] == b"MGPROC02"
+    h = struct.unpack_from("<13i", data, 8)
+    den, iden, fd, fc = struct.unpack_from("<q3d", data, 60)
     prog = program.build_program(4)
-    assert h == (1, 4, 6, 24, len(prog.ops), len(prog.scatter), prog.nslot, prog.nslot_f,
-                 prog.nslot_acc, prog.ncolour_groups, prog.ndiagrams, prog.nterms)
-    off = 56 + 32
+    assert h == (2, 4, 6, 24, len(prog.ops), len(prog.scatter), prog.nslot, prog.nslot_f,
+                 prog.nslot_acc, prog.ncolour_groups, prog.ndiagrams, prog.nterms, 105)
+    off = 60 + 32
     ops = struct.unpack_from(f"<{8 * h[4]}i", data, off)
     off += 32 * h[4]
     assert [list(ops[8 * i:8 * i + 8]) for i in range(h[4])] == [list(r) for r in prog.ops]
@@ -110,5 +124,12 @@ def test_emitter_round_trip(tmp_path):
     off += 8 * 24
     chat, d, perms = colour.colour_matrix(4)
     assert den == d and list(row) == list(chat[0])   # row of the identity ordering
-    assert list(data[off:]) == [v for p in perms for v in p]
+    assert list(data[off:off + 24 * 4]) == [v for p in perms for v in p]
+    off += 24 * 4
+    cho = struct.unpack_from("<106i", data, off)
+    off += 4 * 106
+    chf = struct.unpack_from(f"<{cho[-1]}i", data, off)
+    assert off + 4 * cho[-1] == len(data)
+    assert [[(e >> 3, e & 7) for e in chf[cho[c]:cho[c + 1]]] for c in range(105)] == \
+        [list(ch) for ch in prog.channels]
     assert iden == 512.0 and fd == emit.algorithmic_flops(prog)["diagram"]

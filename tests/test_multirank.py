@@ -57,3 +57,26 @@ def test_two_rank_sharding_and_max_timing():
 
 def test_single_process_timing_is_identity():
     assert bench.max_over_ranks(3.5) == 3.5
+
+
+def test_bench_gpus_flag_launches_the_ranks():
+    """`bench.py --gpus 2` outside a launcher starts two ranks itself
+    (torch.distributed.run, rendezvous on 127.0.0.1); --plan-only makes each
+    rank report its shard over gloo and stop before any GPU work."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items()
+           if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK", "MASTER_ADDR", "MASTER_PORT")}
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--gpus", "2", "--plan-only"],
+                       cwd=root, env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-3000:]
+    lines = [json.loads(ln) for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = lines[0]
+    assert d["n_gpus"] == 2
+    ranks = sorted(d["plan"])
+    assert [x[0] for x in ranks] == [0, 1]
+    assert [x[1] for x in ranks] == [bench.shard_first_candidate(0), bench.shard_first_candidate(1)]
+    assert ranks[0][2] != ranks[1][2]       # different events on the two ranks

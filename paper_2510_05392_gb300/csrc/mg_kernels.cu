@@ -133,24 +133,29 @@ __device__ void run_unit(const Kin<NG> &k, int g, const int4 *__restrict__ ops, 
                     if (!(mode & 8)) break;
                     for (int v = 0; v < 4; v++) amp[v] = ACC[b.z][v];
                 }
+                // jamp updates in pairs: the flows of one scatter list are
+                // distinct, so both old values are loaded before either store
+                // and the two loads wait for memory together
                 const int end = b.x + b.y;
-                for (int s = b.x; s < end; s++) {
-                    const int e = __ldg(scat + s);
-                    const int j = e >> 2;
-                    switch (e & 3) {
-                        case 0:
-                            for (int v = 0; v < 4; v++) J[j][v] = J[j][v] + amp[v];
-                            break;
-                        case 1:
-                            for (int v = 0; v < 4; v++) J[j][v] = J[j][v] - amp[v];
-                            break;
-                        case 2:
-                            for (int v = 0; v < 4; v++) J[j][v] = J[j][v] + mk(-amp[v].i, amp[v].r);
-                            break;
-                        default:
-                            for (int v = 0; v < 4; v++) J[j][v] = J[j][v] + mk(amp[v].i, -amp[v].r);
-                            break;
+                int s = b.x;
+                for (; s + 1 < end; s += 2) {
+                    const int e0 = __ldg(scat + s), e1 = __ldg(scat + s + 1);
+                    cx o0[4], o1[4];
+#pragma unroll
+                    for (int v = 0; v < 4; v++) {
+                        o0[v] = J[e0 >> 2][v];
+                        o1[v] = J[e1 >> 2][v];
                     }
+#pragma unroll
+                    for (int v = 0; v < 4; v++) {
+                        J[e0 >> 2][v] = o0[v] + unit_times(e0, amp[v]);
+                        J[e1 >> 2][v] = o1[v] + unit_times(e1, amp[v]);
+                    }
+                }
+                if (s < end) {
+                    const int e = __ldg(scat + s);
+#pragma unroll
+                    for (int v = 0; v < 4; v++) J[e >> 2][v] = J[e >> 2][v] + unit_times(e, amp[v]);
                 }
                 break;
             }

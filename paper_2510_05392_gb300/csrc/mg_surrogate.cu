@@ -12,12 +12,14 @@
 //             the exact FP64 matrix element is evaluated for those only;
 //             stage 2 keeps u2 < (w/w_hat)/r_max, w = |M|^2 Phi; weight
 //             max(1, w_hat/w_hat_max) * max(1, (w/w_hat)/r_max)
-// GEMMs use the warp-level BF16 tensor-core instructions (WMMA 16x16x16,
-// FP32 accumulate) with bias / SiLU / SiLU' fused into their epilogues; the
-// layers are small, so these kernels are launch- rather than pipe-bound.
+// GEMMs run on the 5th-generation tensor cores (mg_mlp_tc.cu: tcgen05.mma
+// with TMA-fed shared-memory operands and FP32 accumulators in tensor
+// memory) with bias / SiLU / SiLU' fused into their epilogues; the weight
+// gradients are split over the batch and summed in a fixed order.  Every
+// batch is padded to a multiple of 128 rows (zero features, zero loss
+// gradient), so results do not depend on the padding.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
-#include <mma.h>
 #include <stdint.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -25,151 +27,102 @@
 
 #include <vector>
 
+#include "mg_mlp.h"
 #include "mg_process.h"
 #include "mgpu.h"
 #include "mgpu_bench.h"
 #include "mgpu_surrogate.h"
 
-using namespace nvcuda;
-
 namespace {
 
 constexpr int SUR_MAXL = 8;
-constexpr int WM = 16;
+constexpr int WM = 16;     // padding of layer widths
+constexpr int MROWS = 128; // padding of batches (rows of one tensor-core tile)
 
-__device__ __forceinline__ float silu_f(float z) { return z / (1.0f + __expf(-z)); }
-__device__ __forceinline__ float dsilu_f(float z) {
-    const float s = 1.0f / (1.0f + __expf(-z));
-    return s * (1.0f + z * (1.0f - s));
-}
-
-// features: x[i][k] = s_ij / s for pairs i < j (k in pair order), zero padded
-__global__ void k_features(const double *__restrict__ mom, long long n, int npar, int nin,
-                           __nv_bfloat16 *__restrict__ x) {
+// features: x[e][k] = s_ij / s for pairs i < j (k in pair order), zero
+// padded, rows e >= n zero; written row-major [M][nin] and transposed
+// [nin][ldt]
+__global__ void k_features(const double *__restrict__ mom, long long n, long long M, int npar, int nin,
+                           __nv_bfloat16 *__restrict__ x, __nv_bfloat16 *__restrict__ xt, long long ldt) {
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n) return;
-    const double *p = mom + e * npar * 4;
-    const double P0 = p[0] + p[4], P1 = p[1] + p[5], P2 = p[2] + p[6], P3 = p[3] + p[7];
-    const double s = P0 * P0 - P1 * P1 - P2 * P2 - P3 * P3;
+    if (e >= M) return;
     int k = 0;
-    for (int i = 0; i < npar; i++)
-        for (int j = i + 1; j < npar; j++) {
-            const double q0 = p[4 * i] + p[4 * j], q1 = p[4 * i + 1] + p[4 * j + 1];
-            const double q2 = p[4 * i + 2] + p[4 * j + 2], q3 = p[4 * i + 3] + p[4 * j + 3];
-            if (k < nin) x[e * nin + k] = __float2bfloat16_rn((float)((q0 * q0 - q1 * q1 - q2 * q2 - q3 * q3) / s));
-            k++;
-        }
-    for (; k < nin; k++) x[e * nin + k] = __float2bfloat16_rn(0.0f);
-}
-
-// Forward layer: Z[M][N] = A[M][K] W[N][K]^T + b; Aout = silu(Z) (or Z for
-// the output layer).  One warp per 16x16 tile of Z.
-__global__ void k_fwd(const __nv_bfloat16 *__restrict__ A, const __nv_bfloat16 *__restrict__ W,
-                      const float *__restrict__ b, int M, int N, int K, int act,
-                      float *__restrict__ Z, __nv_bfloat16 *__restrict__ Aout) {
-    __shared__ float tile[4][WM * WM];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int t = blockIdx.x * 4 + warp;
-    const int tn = N / WM;
-    if (t >= (M / WM) * tn) return;
-    const int m0 = (t / tn) * WM, n0 = (t % tn) * WM;
-    wmma::fragment<wmma::accumulator, WM, WM, WM, float> c;
-    wmma::fill_fragment(c, 0.0f);
-    for (int k = 0; k < K; k += WM) {
-        wmma::fragment<wmma::matrix_a, WM, WM, WM, __nv_bfloat16, wmma::row_major> fa;
-        wmma::fragment<wmma::matrix_b, WM, WM, WM, __nv_bfloat16, wmma::col_major> fb;
-        wmma::load_matrix_sync(fa, A + (long long)m0 * K + k, K);
-        wmma::load_matrix_sync(fb, W + (long long)n0 * K + k, K);
-        wmma::mma_sync(c, fa, fb, c);
+    if (e < n) {
+        const double *p = mom + e * npar * 4;
+        const double P0 = p[0] + p[4], P1 = p[1] + p[5], P2 = p[2] + p[6], P3 = p[3] + p[7];
+        const double s = P0 * P0 - P1 * P1 - P2 * P2 - P3 * P3;
+        for (int i = 0; i < npar; i++)
+            for (int j = i + 1; j < npar; j++) {
+                const double q0 = p[4 * i] + p[4 * j], q1 = p[4 * i + 1] + p[4 * j + 1];
+                const double q2 = p[4 * i + 2] + p[4 * j + 2], q3 = p[4 * i + 3] + p[4 * j + 3];
+                if (k < nin) {
+                    const __nv_bfloat16 v =
+                        __float2bfloat16_rn((float)((q0 * q0 - q1 * q1 - q2 * q2 - q3 * q3) / s));
+                    x[e * nin + k] = v;
+                    xt[(long long)k * ldt + e] = v;
+                }
+                k++;
+            }
     }
-    wmma::store_matrix_sync(tile[warp], c, WM, wmma::mem_row_major);
-    __syncwarp();
-    for (int q = lane; q < WM * WM; q += 32) {
-        const int r = q / WM, cc = q % WM;
-        const float z = tile[warp][q] + b[n0 + cc];
-        const long long o = (long long)(m0 + r) * N + n0 + cc;
-        if (Z) Z[o] = z;
-        if (Aout) Aout[o] = __float2bfloat16_rn(act ? silu_f(z) : z);
+    for (; k < nin; k++) {
+        x[e * nin + k] = __float2bfloat16_rn(0.0f);
+        xt[(long long)k * ldt + e] = __float2bfloat16_rn(0.0f);
     }
 }
 
-// Backward through a layer's input: dZprev[M][K] = (dZ[M][N] W[N][K]) *
-// silu'(Zprev).  One warp per 16x16 tile.
-__global__ void k_bwd_data(const __nv_bfloat16 *__restrict__ dZ, const __nv_bfloat16 *__restrict__ W,
-                           const float *__restrict__ Zprev, int M, int N, int K,
-                           __nv_bfloat16 *__restrict__ dZprev, float *__restrict__ dZprev32) {
-    __shared__ float tile[4][WM * WM];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int t = blockIdx.x * 4 + warp;
-    const int tk = K / WM;
-    if (t >= (M / WM) * tk) return;
-    const int m0 = (t / tk) * WM, k0 = (t % tk) * WM;
-    wmma::fragment<wmma::accumulator, WM, WM, WM, float> c;
-    wmma::fill_fragment(c, 0.0f);
-    for (int n = 0; n < N; n += WM) {
-        wmma::fragment<wmma::matrix_a, WM, WM, WM, __nv_bfloat16, wmma::row_major> fa;
-        wmma::fragment<wmma::matrix_b, WM, WM, WM, __nv_bfloat16, wmma::row_major> fb;
-        wmma::load_matrix_sync(fa, dZ + (long long)m0 * N + n, N);
-        wmma::load_matrix_sync(fb, W + (long long)n * K + k0, K);
-        wmma::mma_sync(c, fa, fb, c);
-    }
-    wmma::store_matrix_sync(tile[warp], c, WM, wmma::mem_row_major);
-    __syncwarp();
-    for (int q = lane; q < WM * WM; q += 32) {
-        const int r = q / WM, cc = q % WM;
-        const long long o = (long long)(m0 + r) * K + k0 + cc;
-        const float d = tile[warp][q] * dsilu_f(Zprev[o]);
-        dZprev[o] = __float2bfloat16_rn(d);
-        dZprev32[o] = d;
-    }
-}
-
-// Weight gradient: gW[N][K] = dZ[M][N]^T A[M][K] (FP32).  One warp per tile.
-__global__ void k_bwd_weight(const __nv_bfloat16 *__restrict__ dZ, const __nv_bfloat16 *__restrict__ A,
-                             int M, int N, int K, float *__restrict__ gW) {
-    const int warp = threadIdx.x >> 5;
-    const int t = blockIdx.x * 4 + warp;
-    const int tk = K / WM;
-    if (t >= (N / WM) * tk) return;
-    const int n0 = (t / tk) * WM, k0 = (t % tk) * WM;
-    wmma::fragment<wmma::accumulator, WM, WM, WM, float> c;
-    wmma::fill_fragment(c, 0.0f);
-    for (int m = 0; m < M; m += WM) {
-        wmma::fragment<wmma::matrix_a, WM, WM, WM, __nv_bfloat16, wmma::col_major> fa;
-        wmma::fragment<wmma::matrix_b, WM, WM, WM, __nv_bfloat16, wmma::row_major> fb;
-        wmma::load_matrix_sync(fa, dZ + (long long)m * N + n0, N);
-        wmma::load_matrix_sync(fb, A + (long long)m * K + k0, K);
-        wmma::mma_sync(c, fa, fb, c);
-    }
-    wmma::store_matrix_sync(gW + (long long)n0 * K + k0, c, K, wmma::mem_row_major);
+// gW[i] = sum over the splits of the weight-gradient partials, fixed order
+__global__ void k_wgrad_reduce(const float *__restrict__ part, int nsplit, long long n,
+                               float *__restrict__ gW) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float s = 0.0f;
+    for (int k = 0; k < nsplit; k++) s += part[(long long)k * n + i];
+    gW[i] = s;
 }
 
 // gb[n] = sum_m dZ[m][n] from the FP32 values (the BF16 copies feed the
-// weight-gradient GEMM; their rounding would not cancel in this sum)
-__global__ void k_bias_grad(const float *__restrict__ dZ, int M, int N, float *__restrict__ gb) {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
+// weight-gradient GEMM; their rounding would not cancel in this sum): 32
+// columns per block, 8 row slices per column summed in FP64 and added in a
+// fixed order
+__global__ void k_bias_grad(const float *__restrict__ dZ, long long M, int N, float *__restrict__ gb) {
+    __shared__ double red[8][32];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int n = blockIdx.x * 32 + tx;
     double s = 0.0;
-    for (int m = 0; m < M; m++) s += dZ[(long long)m * N + n];
-    gb[n] = (float)s;
+    if (n < N)
+        for (long long m = ty; m < M; m += 8) s += dZ[m * N + n];
+    red[ty][tx] = s;
+    __syncthreads();
+    if (ty == 0 && n < N) {
+        double t = 0.0;
+        for (int k = 0; k < 8; k++) t += red[k][tx];
+        gb[n] = (float)t;
+    }
 }
 
-// Output-layer loss gradient: dZ[m][0] = 2 (f_m - y_m) / M (other padded
-// columns 0); per-block partial sums of the squared error.
-__global__ void k_loss(const float *__restrict__ Zout, int M, int N, const float *__restrict__ y,
-                       __nv_bfloat16 *__restrict__ dZ, float *__restrict__ dZ32,
+// Output-layer loss gradient: dZ[m][0] = 2 (f_m - y_m) / nvalid for rows
+// m < nvalid, 0 elsewhere (padded columns and rows), row-major [M][N], its
+// transpose [N][ldt] and an FP32 copy; per-block partial sums of the squared
+// error.
+__global__ void k_loss(const float *__restrict__ Zout, long long M, int nvalid, int N,
+                       const float *__restrict__ y, __nv_bfloat16 *__restrict__ dZ,
+                       __nv_bfloat16 *__restrict__ dZT, long long ldt, float *__restrict__ dZ32,
                        double *__restrict__ part) {
     __shared__ double red[256];
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double se = 0.0;
     if (m < M) {
-        const float d = Zout[(long long)m * N] - y[m];
-        se = (double)d * d;
-        dZ[(long long)m * N] = __float2bfloat16_rn(2.0f * d / M);
-        dZ32[(long long)m * N] = 2.0f * d / M;
-        for (int c = 1; c < N; c++) {
-            dZ[(long long)m * N + c] = __float2bfloat16_rn(0.0f);
-            dZ32[(long long)m * N + c] = 0.0f;
+        float g = 0.0f;
+        if (m < nvalid) {
+            const float d = Zout[m * N] - y[m];
+            se = (double)d * d;
+            g = 2.0f * d / nvalid;
+        }
+        for (int c = 0; c < N; c++) {
+            const float v = c == 0 ? g : 0.0f;
+            dZ[m * N + c] = __float2bfloat16_rn(v);
+            dZT[(long long)c * ldt + m] = __float2bfloat16_rn(v);
+            dZ32[m * N + c] = v;
         }
     }
     red[threadIdx.x] = se;
@@ -181,13 +134,15 @@ __global__ void k_loss(const float *__restrict__ Zout, int M, int N, const float
     if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
-// Adam on FP32 master parameters (rows >= nrow_real of a padded output layer
-// stay zero: their gradients are zero), BF16 copy refreshed.
+// Adam on FP32 master parameters [rows][cols] (rows >= the real output width
+// of a padded layer stay zero: their gradients are zero); BF16 copies
+// refreshed, row-major and (when given) transposed [cols][rows].
 __global__ void k_adam(float *__restrict__ p, float *__restrict__ m, float *__restrict__ v,
-                       const float *__restrict__ g, __nv_bfloat16 *__restrict__ p16, long long n,
-                       float lr, float b1, float b2, float eps, float c1, float c2) {
+                       const float *__restrict__ g, __nv_bfloat16 *__restrict__ p16,
+                       __nv_bfloat16 *__restrict__ p16t, int rows, int cols, float lr, float b1,
+                       float b2, float eps, float c1, float c2) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= (long long)rows * cols) return;
     const float gi = g[i];
     const float mi = b1 * m[i] + (1.0f - b1) * gi;
     const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
@@ -196,6 +151,7 @@ __global__ void k_adam(float *__restrict__ p, float *__restrict__ m, float *__re
     const float w = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
     p[i] = w;
     if (p16) p16[i] = __float2bfloat16_rn(w);
+    if (p16t) p16t[(i % cols) * rows + i / cols] = __float2bfloat16_rn(w);
 }
 
 // target: y = (log me - mu) / sigma, with mu/sigma from k_logstats
@@ -319,16 +275,21 @@ struct mg_surrogate {
     int in[SUR_MAXL], out[SUR_MAXL], outp[SUR_MAXL];   // sizes (outp: padded to 16)
     float *W[SUR_MAXL], *b[SUR_MAXL], *gW[SUR_MAXL], *gb[SUR_MAXL];
     float *mW[SUR_MAXL], *vW[SUR_MAXL], *mb[SUR_MAXL], *vb[SUR_MAXL];
-    __nv_bfloat16 *W16[SUR_MAXL];
+    __nv_bfloat16 *W16[SUR_MAXL];    // [outp][in]  BF16 copy of W
+    __nv_bfloat16 *WT16[SUR_MAXL];   // [in][outp]  BF16 copy of W^T
     int t;                       // Adam steps taken
-    int bmax;                    // rows per forward/backward chunk
-    __nv_bfloat16 *A[SUR_MAXL + 1];  // activations (A[0] = features)
-    float *Z[SUR_MAXL];
-    __nv_bfloat16 *dZ[SUR_MAXL];
-    float *dZ32[SUR_MAXL];
+    int bmax;                    // rows per forward/backward chunk (multiple of 128)
+    __nv_bfloat16 *A[SUR_MAXL + 1];  // activations [bmax][in_l] (A[0] = features)
+    __nv_bfloat16 *AT[SUR_MAXL + 1]; // the same transposed, [in_l][bmax]
+    float *Z[SUR_MAXL];              // pre-activations [bmax][outp]
+    __nv_bfloat16 *dZ[SUR_MAXL];     // loss gradients [bmax][outp]
+    __nv_bfloat16 *dZT[SUR_MAXL];    // the same transposed, [outp][bmax]
+    float *dZ32[SUR_MAXL];           // FP32 copy (bias gradients)
+    float *wpart;                    // weight-gradient partials [split][outp][in]
     double *ms;                  // mu, sigma of log|M|^2 (device)
     double *part;                // loss partial sums
     float *y;                    // standardised targets of a chunk
+    int *err;                    // device error word of the bounded waits
 };
 
 namespace {
@@ -346,47 +307,120 @@ void free_sur(mg_surrogate *s) {
     for (int l = 0; l < SUR_MAXL; l++) {
         cudaFree(s->W[l]); cudaFree(s->b[l]); cudaFree(s->gW[l]); cudaFree(s->gb[l]);
         cudaFree(s->mW[l]); cudaFree(s->vW[l]); cudaFree(s->mb[l]); cudaFree(s->vb[l]);
-        cudaFree(s->W16[l]); cudaFree(s->Z[l]); cudaFree(s->dZ[l]); cudaFree(s->dZ32[l]);
+        cudaFree(s->W16[l]); cudaFree(s->WT16[l]); cudaFree(s->Z[l]); cudaFree(s->dZ[l]);
+        cudaFree(s->dZT[l]); cudaFree(s->dZ32[l]);
     }
-    for (int l = 0; l <= SUR_MAXL; l++) cudaFree(s->A[l]);
-    cudaFree(s->ms); cudaFree(s->part); cudaFree(s->y);
+    for (int l = 0; l <= SUR_MAXL; l++) {
+        cudaFree(s->A[l]);
+        cudaFree(s->AT[l]);
+    }
+    cudaFree(s->wpart); cudaFree(s->ms); cudaFree(s->part); cudaFree(s->y); cudaFree(s->err);
     delete s;
 }
 
 int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
 
-// forward pass over rows [0, M) of s->A[0]
-int forward(mg_surrogate *s, int M, cudaStream_t st) {
+long long pad_rows(long long m) { return (m + MROWS - 1) / MROWS * MROWS; }
+
+// column tile of a GEMM with N output columns (a multiple of 16)
+int pick_nt(int N) {
+    for (int nt = 64; nt >= 16; nt >>= 1)
+        if (N % nt == 0) return nt;
+    return 16;
+}
+
+// weight-gradient splits of a batch of M rows (64-row K chunks, 4 per split)
+int wsplits(long long M) {
+    const long long ch = M / 64;
+    return (int)(ch % 4 == 0 ? ch / 4 : ch / 2);
+}
+
+// forward pass over rows [0, M) of s->A[0] (M a multiple of 128)
+int forward(mg_surrogate *s, long long M, cudaStream_t st) {
     for (int l = 0; l < s->nl; l++) {
-        const int tiles = (M / WM) * (s->outp[l] / WM);
         const bool last = (l == s->nl - 1);
+        mg_mlp_epi ep;
+        memset(&ep, 0, sizeof(ep));
+        ep.bias = s->b[l];
+        ep.Z = s->Z[l];
+        ep.A = last ? nullptr : s->A[l + 1];
+        ep.AT = last ? nullptr : s->AT[l + 1];
+        ep.ldz = s->outp[l];
+        ep.ldt = s->bmax;
+        ep.m_valid = (int)M;
+        ep.n_valid = s->outp[l];
+        SCHECK(mg_launch_mlp_gemm(last ? MG_MLP_FWD_OUT : MG_MLP_FWD, s->A[l], M, s->in[l], s->W16[l],
+                                  s->outp[l], s->in[l], s->in[l], M, s->outp[l], pick_nt(s->outp[l]), 1,
+                                  ep, s->err, st));
+    }
+    return MG_OK;
+}
+
+// backward pass (needs forward + k_loss): fills gW, gb
+int backward(mg_surrogate *s, long long M, cudaStream_t st) {
+    const int ns = wsplits(M);
+    for (int l = s->nl - 1; l >= 0; l--) {
+        mg_mlp_epi ep;
+        memset(&ep, 0, sizeof(ep));
+        ep.part = s->wpart;
+        ep.ldz = s->in[l];
+        ep.m_valid = s->outp[l];
+        ep.n_valid = s->in[l];
+        // gW[n][k] = sum_m dZ[m][n] A[m][k]: X = dZ^T [outp][batch], Y = A^T [in][batch]
+        SCHECK(mg_launch_mlp_gemm(MG_MLP_WGRAD, s->dZT[l], s->outp[l], s->bmax, s->AT[l], s->in[l],
+                                  s->bmax, (int)M, pad_rows(s->outp[l]), s->in[l], pick_nt(s->in[l]), ns,
+                                  ep, s->err, st));
+        const long long nw = (long long)s->outp[l] * s->in[l];
         mg_note_launch();
-        k_fwd<<<blocks_for(tiles, 4), 128, 0, st>>>(s->A[l], s->W16[l], s->b[l], M, s->outp[l],
-                                                   s->in[l], last ? 0 : 1, s->Z[l],
-                                                   last ? nullptr : s->A[l + 1]);
+        k_wgrad_reduce<<<blocks_for(nw, 256), 256, 0, st>>>(s->wpart, ns, nw, s->gW[l]);
+        mg_note_launch();
+        k_bias_grad<<<blocks_for(s->outp[l], 32), 256, 0, st>>>(s->dZ32[l], M, s->outp[l], s->gb[l]);
+        if (l > 0) {
+            // dZ_l-1 = (dZ_l W_l) * silu'(Z_l-1): X = dZ_l [batch][outp], Y = W_l^T [in][outp]
+            mg_mlp_epi ed;
+            memset(&ed, 0, sizeof(ed));
+            ed.Zprev = s->Z[l - 1];
+            ed.dZ = s->dZ[l - 1];
+            ed.dZT = s->dZT[l - 1];
+            ed.dZ32 = s->dZ32[l - 1];
+            ed.ldz = s->in[l];
+            ed.ldt = s->bmax;
+            ed.m_valid = (int)M;
+            ed.n_valid = s->in[l];
+            SCHECK(mg_launch_mlp_gemm(MG_MLP_BWD_DATA, s->dZ[l], M, s->outp[l], s->WT16[l], s->in[l],
+                                      s->outp[l], s->outp[l], M, s->in[l], pick_nt(s->in[l]), 1, ed,
+                                      s->err, st));
+        }
     }
     SCHECK(cudaGetLastError());
     return MG_OK;
 }
 
-// backward pass (needs forward + k_loss): fills gW, gb
-int backward(mg_surrogate *s, int M, cudaStream_t st) {
-    for (int l = s->nl - 1; l >= 0; l--) {
-        const int tiles_w = (s->outp[l] / WM) * (s->in[l] / WM);
-        mg_note_launch();
-        k_bwd_weight<<<blocks_for(tiles_w, 4), 128, 0, st>>>(s->dZ[l], s->A[l], M, s->outp[l],
-                                                            s->in[l], s->gW[l]);
-        mg_note_launch();
-        k_bias_grad<<<blocks_for(s->outp[l], 128), 128, 0, st>>>(s->dZ32[l], M, s->outp[l], s->gb[l]);
-        if (l > 0) {
-            const int tiles_d = (M / WM) * (s->in[l] / WM);
-            mg_note_launch();
-            k_bwd_data<<<blocks_for(tiles_d, 4), 128, 0, st>>>(s->dZ[l], s->W16[l], s->Z[l - 1], M,
-                                                              s->outp[l], s->in[l], s->dZ[l - 1],
-                                                              s->dZ32[l - 1]);
-        }
+// status of the bounded waits so far (synchronises the stream; clears it)
+int device_status(mg_surrogate *s, cudaStream_t st) {
+    int h = 0;
+    SCHECK(cudaMemcpyAsync(&h, s->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SCHECK(cudaStreamSynchronize(st));
+    if (h) {
+        SCHECK(cudaMemsetAsync(s->err, 0, sizeof(int), st));
+        return MG_ERR_DEVICE_TIMEOUT;
     }
-    SCHECK(cudaGetLastError());
+    return MG_OK;
+}
+
+// BF16 copies of W ([outp][in]) and W^T ([in][outp]) from FP32 host values
+// (rows >= out zero)
+int upload_w16(mg_surrogate *s, int l, const float *w) {
+    const int ro = s->outp[l], ci = s->in[l];
+    std::vector<__nv_bfloat16> w16((size_t)ro * ci), wt((size_t)ro * ci);
+    for (int r = 0; r < ro; r++)
+        for (int c = 0; c < ci; c++) {
+            const __nv_bfloat16 v = __float2bfloat16_rn(r < s->out[l] ? w[(size_t)r * ci + c] : 0.0f);
+            w16[(size_t)r * ci + c] = v;
+            wt[(size_t)c * ro + r] = v;
+        }
+    SCHECK(cudaMemcpy(s->W16[l], w16.data(), w16.size() * 2, cudaMemcpyHostToDevice));
+    SCHECK(cudaMemcpy(s->WT16[l], wt.data(), wt.size() * 2, cudaMemcpyHostToDevice));
     return MG_OK;
 }
 
@@ -402,11 +436,14 @@ int mg_sur_create(int nin, int hidden, int nhidden, uint64_t seed, int bmax, mg_
     mg_surrogate *s = new mg_surrogate();
     memset(s, 0, sizeof(*s));
     s->nl = nhidden + 1;
-    s->bmax = bmax;
+    s->bmax = (int)pad_rows(bmax);
+    bmax = s->bmax;
+    int wmax = 0;
     for (int l = 0; l < s->nl; l++) {
         s->in[l] = (l == 0) ? nin : hidden;
         s->out[l] = (l == s->nl - 1) ? 1 : hidden;
         s->outp[l] = (s->out[l] + WM - 1) / WM * WM;
+        if (s->outp[l] * s->in[l] > wmax) wmax = s->outp[l] * s->in[l];
     }
     // Glorot-uniform initial weights from a seeded generator (host), biases 0
     uint64_t st = seed * 6364136223846793005ULL + 1442695040888963407ULL;
@@ -421,8 +458,6 @@ int mg_sur_create(int nin, int hidden, int nhidden, uint64_t seed, int bmax, mg_
         const double lim = sqrt(6.0 / (s->in[l] + s->out[l]));
         for (int r = 0; r < s->out[l]; r++)
             for (int c = 0; c < s->in[l]; c++) w[(size_t)r * s->in[l] + c] = (float)((2 * uni() - 1) * lim);
-        std::vector<__nv_bfloat16> w16(nw);
-        for (size_t i = 0; i < nw; i++) w16[i] = __float2bfloat16_rn(w[i]);
         cudaError_t e = cudaSuccess;
         float **f[] = {&s->W[l], &s->gW[l], &s->mW[l], &s->vW[l]};
         for (auto p : f)
@@ -431,19 +466,27 @@ int mg_sur_create(int nin, int hidden, int nhidden, uint64_t seed, int bmax, mg_
         for (auto p : g)
             if (e == cudaSuccess && (e = cudaMalloc(p, nb * 4)) == cudaSuccess) e = cudaMemset(*p, 0, nb * 4);
         if (e == cudaSuccess) e = cudaMalloc(&s->W16[l], nw * 2);
+        if (e == cudaSuccess) e = cudaMalloc(&s->WT16[l], nw * 2);
         if (e == cudaSuccess) e = cudaMemcpy(s->W[l], w.data(), nw * 4, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(s->W16[l], w16.data(), nw * 2, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMalloc(&s->Z[l], (size_t)bmax * s->outp[l] * 4);
         if (e == cudaSuccess) e = cudaMalloc(&s->dZ[l], (size_t)bmax * s->outp[l] * 2);
+        if (e == cudaSuccess) e = cudaMalloc(&s->dZT[l], (size_t)bmax * s->outp[l] * 2);
         if (e == cudaSuccess) e = cudaMalloc(&s->dZ32[l], (size_t)bmax * s->outp[l] * 4);
         if (e == cudaSuccess) e = cudaMalloc(&s->A[l + 1], (size_t)bmax * s->outp[l] * 2);
+        if (e == cudaSuccess) e = cudaMalloc(&s->AT[l + 1], (size_t)bmax * s->outp[l] * 2);
         if (e != cudaSuccess) rc = sur_fail(e);
+        if (rc == MG_OK) rc = upload_w16(s, l, w.data());
     }
     if (rc == MG_OK) {
         cudaError_t e = cudaMalloc(&s->A[0], (size_t)bmax * nin * 2);
+        if (e == cudaSuccess) e = cudaMalloc(&s->AT[0], (size_t)bmax * nin * 2);
+        // at most bmax / 128 splits (2 chunks of 64 rows each) for any batch
+        if (e == cudaSuccess) e = cudaMalloc(&s->wpart, (size_t)(bmax / 128) * wmax * 4);
         if (e == cudaSuccess) e = cudaMalloc(&s->ms, 2 * sizeof(double));
         if (e == cudaSuccess) e = cudaMalloc(&s->part, (size_t)(bmax / 256 + 1) * sizeof(double));
         if (e == cudaSuccess) e = cudaMalloc(&s->y, (size_t)bmax * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&s->err, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(s->err, 0, sizeof(int));
         const double ms0[2] = {0.0, 1.0};
         if (e == cudaSuccess) e = cudaMemcpy(s->ms, ms0, sizeof(ms0), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) rc = sur_fail(e);
@@ -480,11 +523,12 @@ static int copy_params(mg_surrogate *s, float *host, int to_host, int grads) {
         } else {
             e = cudaMemcpy(W, host + off, nw * 4, cudaMemcpyHostToDevice);
             if (e == cudaSuccess) e = cudaMemcpy(b, host + off + nw, s->out[l] * 4, cudaMemcpyHostToDevice);
-            std::vector<__nv_bfloat16> w16((size_t)s->outp[l] * s->in[l], __float2bfloat16_rn(0.0f));
-            for (size_t i = 0; i < nw; i++) w16[i] = __float2bfloat16_rn(host[off + i]);
-            if (e == cudaSuccess) e = cudaMemcpy(s->W16[l], w16.data(), w16.size() * 2, cudaMemcpyHostToDevice);
         }
         if (e != cudaSuccess) return sur_fail(e);
+        if (!to_host) {
+            const int rc = upload_w16(s, l, host + off);
+            if (rc) return rc;
+        }
         off += nw + s->out[l];
     }
     return MG_OK;
@@ -542,24 +586,28 @@ int mg_sur_get_target_stats(mg_surrogate *s, double *mu_sigma) {
 
 // Loss and gradients for one batch (rows of momenta [m][npar][4] with
 // targets y_dev[m] = standardised log|M|^2, FP32); m multiple of 16, <= bmax.
+// The batch is padded to a multiple of 128 rows with zero features and zero
+// loss gradient.
 int mg_sur_loss_grad(mg_surrogate *s, const double *mom, int npar, const float *y, int m,
                      double *loss_out, void *stream) {
     if (!s || !mom || !y || m < 16 || m % 16 || m > s->bmax || npar < 2) return MG_ERR_BAD_ARG;
     cudaStream_t st = (cudaStream_t)stream;
+    const long long M = pad_rows(m);
     mg_note_launch();
-    k_features<<<blocks_for(m, 128), 128, 0, st>>>(mom, m, npar, s->in[0], s->A[0]);
-    int rc = forward(s, m, st);
+    k_features<<<blocks_for(M, 128), 128, 0, st>>>(mom, m, M, npar, s->in[0], s->A[0], s->AT[0], s->bmax);
+    int rc = forward(s, M, st);
     if (rc) return rc;
-    const int nb = blocks_for(m, 256);
+    const int nb = blocks_for(M, 256);
     mg_note_launch();
-    k_loss<<<nb, 256, 0, st>>>(s->Z[s->nl - 1], m, s->outp[s->nl - 1], y, s->dZ[s->nl - 1],
-                               s->dZ32[s->nl - 1], s->part);
-    rc = backward(s, m, st);
+    k_loss<<<nb, 256, 0, st>>>(s->Z[s->nl - 1], M, m, s->outp[s->nl - 1], y, s->dZ[s->nl - 1],
+                               s->dZT[s->nl - 1], s->bmax, s->dZ32[s->nl - 1], s->part);
+    rc = backward(s, M, st);
     if (rc) return rc;
     if (loss_out) {
         std::vector<double> h(nb);
         SCHECK(cudaMemcpyAsync(h.data(), s->part, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
-        SCHECK(cudaStreamSynchronize(st));
+        rc = device_status(s, st);
+        if (rc) return rc;
         double t = 0.0;
         for (double v : h) t += v;
         *loss_out = t / m;
@@ -576,11 +624,13 @@ int mg_sur_adam(mg_surrogate *s, double lr, void *stream) {
     for (int l = 0; l < s->nl; l++) {
         const long long nw = (long long)s->outp[l] * s->in[l];
         mg_note_launch();
-        k_adam<<<blocks_for(nw, 256), 256, 0, st>>>(s->W[l], s->mW[l], s->vW[l], s->gW[l], s->W16[l], nw,
-                                                   (float)lr, b1, b2, 1e-8f, c1, c2);
+        k_adam<<<blocks_for(nw, 256), 256, 0, st>>>(s->W[l], s->mW[l], s->vW[l], s->gW[l], s->W16[l],
+                                                   s->WT16[l], s->outp[l], s->in[l], (float)lr, b1, b2,
+                                                   1e-8f, c1, c2);
         mg_note_launch();
         k_adam<<<blocks_for(s->outp[l], 256), 256, 0, st>>>(s->b[l], s->mb[l], s->vb[l], s->gb[l], nullptr,
-                                                           s->outp[l], (float)lr, b1, b2, 1e-8f, c1, c2);
+                                                           nullptr, 1, s->outp[l], (float)lr, b1, b2,
+                                                           1e-8f, c1, c2);
     }
     SCHECK(cudaGetLastError());
     return MG_OK;
@@ -609,6 +659,8 @@ int mg_sur_train(mg_surrogate *s, const double *mom, int npar, const double *me,
             if (rc) return rc;
         }
     }
+    const int rc = device_status(s, st);
+    if (rc) return rc;
     if (last_epoch_loss) *last_epoch_loss = acc / (double)nbatch;
     return MG_OK;
 }
@@ -620,11 +672,10 @@ int mg_sur_predict(mg_surrogate *s, const double *mom, int npar, int64_t n, doub
     cudaStream_t st = (cudaStream_t)stream;
     for (int64_t e0 = 0; e0 < n; e0 += s->bmax) {
         const int64_t c = (n - e0 < s->bmax) ? n - e0 : s->bmax;
-        const int M = (int)((c + WM - 1) / WM * WM);
+        const long long M = pad_rows(c);
         mg_note_launch();
-        k_features<<<blocks_for(c, 128), 128, 0, st>>>(mom + e0 * npar * 4, c, npar, s->in[0], s->A[0]);
-        if (M > c)
-            SCHECK(cudaMemsetAsync(s->A[0] + c * s->in[0], 0, (size_t)(M - c) * s->in[0] * 2, st));
+        k_features<<<blocks_for(M, 128), 128, 0, st>>>(mom + e0 * npar * 4, c, M, npar, s->in[0], s->A[0],
+                                                      s->AT[0], s->bmax);
         int rc = forward(s, M, st);
         if (rc) return rc;
         mg_note_launch();
@@ -686,11 +737,7 @@ int mg_sur_load(mg_surrogate *s, const char *path) {
             std::vector<float> h(len[k]);
             if (fread(h.data(), 4, len[k], f) != len[k]) rc = MG_ERR_BAD_ARG;
             else if (cudaMemcpy(arr[k], h.data(), len[k] * 4, cudaMemcpyHostToDevice) != cudaSuccess) rc = MG_ERR_CUDA;
-            if (!rc && k == 0) {
-                std::vector<__nv_bfloat16> w16(nw);
-                for (size_t i = 0; i < nw; i++) w16[i] = __float2bfloat16_rn(h[i]);
-                if (cudaMemcpy(s->W16[l], w16.data(), nw * 2, cudaMemcpyHostToDevice) != cudaSuccess) rc = MG_ERR_CUDA;
-            }
+            if (!rc && k == 0) rc = upload_w16(s, l, h.data());
         }
     }
     if (!rc) {

@@ -72,14 +72,17 @@ def _bf16(a):
     return t.to(torch.float64).numpy()
 
 
-def test_gradients_match_cpu_oracle():
+@pytest.mark.parametrize("m", [512, 400])
+def test_gradients_match_cpu_oracle(m):
+    """Gradients of every layer against the CPU oracle (FP64 with the GPU's
+    BF16 rounding points); m = 400 is padded to 512 rows inside the library
+    (zero features, zero loss gradient), which must not change them."""
     L = _lib()
     h = _new(L)
     n = ctypes.c_int64()
     L.mg_sur_param_count(h, ctypes.byref(n))
     flat = np.zeros(n.value, dtype=np.float32)
     L.mg_sur_get_params(h, flat.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
-    m = 512
     mom = ps.generate(m, 2, 1500.0, 77, ptmin=20.0, drmin=0.4)
     y = np.random.default_rng(0).normal(size=m).astype(np.float32)
     loss = ctypes.c_double()
@@ -112,6 +115,51 @@ def test_gradients_match_cpu_oracle():
     assert max(errs[(l, 0)] for l in range(4)) < 2e-3, errs
     assert max(errs[(l, 1)] for l in range(4)) < 5e-3, errs
     assert max(errs_exact[(l, 0)] for l in range(4)) < 3e-2
+
+
+def test_forward_layers_on_tensor_cores():
+    """Each layer's tensor-core GEMM against the same contraction in FP64 of
+    the BF16 values it read (activations from the debug export, BF16-rounded
+    weights): Z_l = A_l W_l^T + b_l to FP32 accumulation accuracy, and
+    A_l+1 = silu(Z_l) rounded to BF16 (one BF16 step allowed for the fast
+    exponential).  Pins the operand layouts, swizzle, descriptors, column
+    tiles and the epilogue's row/column mapping."""
+    L = _lib()
+    L.mg_sur_debug_buffer.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_float)]
+    h = _new(L, seed=11)
+    n = ctypes.c_int64()
+    L.mg_sur_param_count(h, ctypes.byref(n))
+    flat = np.zeros(n.value, dtype=np.float32)
+    L.mg_sur_get_params(h, flat.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+    params = _flat_to_params(flat)
+    m = 384
+    mom = ps.generate(m, 2, 1500.0, 78, ptmin=20.0, drmin=0.4)
+    y = np.zeros(m, dtype=np.float32)
+    md, yd = torch.from_numpy(mom).cuda(), torch.from_numpy(y).cuda()
+    assert L.mg_sur_loss_grad(h, ctypes.c_void_p(md.data_ptr()), 6, ctypes.c_void_p(yd.data_ptr()), m,
+                              None, _stream()) == 0
+    torch.cuda.synchronize()
+    widths = [32, 256, 256, 256]
+    outp = [256, 256, 256, 16]
+
+    def buf(which, layer, cols):
+        a = np.zeros(m * cols, dtype=np.float32)
+        assert L.mg_sur_debug_buffer(h, which, layer, m, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))) == 0
+        return a.reshape(m, cols).astype(np.float64)
+
+    for l in range(4):
+        A = buf(0, l, widths[l])
+        Z = buf(1, l, outp[l])[:, :SIZES[l + 1]]
+        W = S.round_bf16(params[l][0])
+        ref = A @ W.T + params[l][1]
+        scale = np.abs(A) @ np.abs(W).T + np.abs(params[l][1])
+        assert (np.abs(Z - ref) <= 1e-5 * scale + 1e-30).all(), l
+        if l < 3:
+            An = buf(0, l + 1, widths[l + 1])
+            sil = Z / (1 + np.exp(-Z))
+            assert (np.abs(An - _bf16(sil)) <= 2 ** -7 * np.abs(sil) + 1e-30).all(), l
+    L.mg_sur_destroy(h)
 
 
 def _train_set(ng, n, seed, sqrts=1500.0):

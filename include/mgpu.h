@@ -142,7 +142,10 @@ int mg_filter_helicities(mg_process *p, const double *momenta_dev, int64_t n, vo
  * looks up the array's device address (make it before any stream capture);
  * the current device must be the process's device.  All calls share the
  * array: calls whose work overlaps on the GPU (other threads, other streams)
- * race and must be serialised by the caller.  Synchronises the stream. */
+ * race and must be serialised by the caller.  Its uploads of the helicity
+ * list are ordered on `stream` (none goes through the legacy default
+ * stream); like every call on a process it must not overlap that process's
+ * other work on the GPU.  Synchronises the stream. */
 int mg_filter_helicities_noalloc(mg_process *p, const double *momenta_dev, int64_t n, void *stream,
                                  int *ngood_out);
 
@@ -251,7 +254,10 @@ void mg_process_destroy(mg_process *p);
  *
  * mg_batch_create records the blocks (device pointers momenta[i]
  * [nevt[i]][npar_i][4] and me_out[i] [nevt[i]], owned by the caller and read
- * on every run); mg_batch_run replays the launch as a CUDA graph (captured on
+ * on every run) and copies each process's current helicity list (a later
+ * mg_filter_helicities of a process does not change the batch); the batch
+ * reads its processes' device tables on every run, so it must be destroyed
+ * before any of them; mg_batch_run replays the launch as a CUDA graph (captured on
  * the first run on a private stream, asynchronous on `stream` afterwards);
  * mg_batch_autotune times the batch for several threads-per-event choices of
  * every block and CTAs per SM (coordinate descent, `reps` launches each,

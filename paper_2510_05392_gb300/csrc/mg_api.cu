@@ -115,8 +115,9 @@ void free_proc(mg_process *p) {
 
 // Good-helicity mask -> work units: one per gluon-helicity configuration g
 // that has a good helicity, with the 4-bit mask of its good (top, antitop)
-// combinations (bit 2*bt + btb).
-int set_hel_list(mg_process *p, const uint8_t *mask) {
+// combinations (bit 2*bt + btb).  The upload is a plain cudaMemcpy, or, with
+// async, a cudaMemcpyAsync ordered on stream s.
+int set_hel_list(mg_process *p, const uint8_t *mask, bool async = false, cudaStream_t s = nullptr) {
     const int npar = p->tab->npar, ng = p->tab->ngluon;
     int units[128];
     int nu = 0, ngood = 0;
@@ -136,7 +137,10 @@ int set_hel_list(mg_process *p, const uint8_t *mask) {
         }
         if (m) units[nu++] = (g << 4) | m;
     }
-    if (nu > 0) MG_CUDA(cudaMemcpy(p->d_units, units, sizeof(int) * nu, cudaMemcpyHostToDevice));
+    if (nu > 0 && async)
+        MG_CUDA(cudaMemcpyAsync(p->d_units, units, sizeof(int) * nu, cudaMemcpyHostToDevice, s));
+    else if (nu > 0)
+        MG_CUDA(cudaMemcpy(p->d_units, units, sizeof(int) * nu, cudaMemcpyHostToDevice));
     p->nunits = nu;
     p->ngood = ngood;
     return MG_OK;
@@ -1043,7 +1047,8 @@ extern "C" int mg_filter_helicities_noalloc(mg_process *p, const double *mom, in
     unsigned char *dmask = (unsigned char *)scratch + MG_NOALLOC_FILTER_MAX_EVENTS * 256 * sizeof(double);
     uint8_t all[512];
     memset(all, 1, sizeof(all));
-    st = set_hel_list(p, all);
+    // unit-list uploads ordered on the caller's stream (no legacy-stream copy)
+    st = set_hel_list(p, all, true, s);
     if (st) return st;
     uint8_t mask[512];
     // the array keeps the previous call's contents: clear what is read
@@ -1058,8 +1063,10 @@ extern "C" int mg_filter_helicities_noalloc(mg_process *p, const double *mom, in
         p->ngood = -1;
         return cuda_fail(e);
     }
-    st = set_hel_list(p, mask);
+    st = set_hel_list(p, mask, true, s);
     if (st) return st;
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e);
     if (ngood_out) *ngood_out = p->ngood;
     return MG_OK;
 }

@@ -26,6 +26,7 @@ struct mg_batch {
     std::vector<mg_batch_item> items;   // host copy, sorted heaviest first
     std::vector<int> order;             // items[k] came from caller index order[k]
     mg_batch_item *d_items;
+    int *d_units;                       // the blocks' work-unit lists, copied at creation
     unsigned long long *d_counter;
     long long total_slots;
     int nsm, ctas_per_sm, max_ctas_per_sm;
@@ -74,6 +75,7 @@ void free_batch(mg_batch *b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     cudaFree(b->d_items);
+    cudaFree(b->d_units);
     cudaFree(b->d_counter);
     delete b;
 }
@@ -158,6 +160,15 @@ int mg_batch_create(int nproc, mg_process *const *procs, const double *const *mo
     b->ctas_per_sm = b->max_ctas_per_sm;
     cudaError_t e = cudaMalloc(&b->d_items, sizeof(mg_batch_item) * nproc);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(unsigned long long));
+    // the batch's own copy of every block's work-unit list (at most 128 units
+    // each), so that a later helicity filter of a process does not change the
+    // captured launch under it
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_units, sizeof(int) * 128 * nproc);
+    for (int k = 0; e == cudaSuccess && k < nproc; k++) {
+        e = cudaMemcpy(b->d_units + 128 * k, b->items[k].units, sizeof(int) * b->items[k].nunits,
+                       cudaMemcpyDeviceToDevice);
+        b->items[k].units = b->d_units + 128 * k;
+    }
     if (e != cudaSuccess) {
         free_batch(b);
         return e == cudaErrorMemoryAllocation ? MG_ERR_NO_MEMORY : mg_cuda_fail(e);

@@ -61,6 +61,21 @@ def test_noalloc_filter_matches_allocating_filter(ng_final, sqrts):
         assert rel <= 1e-9
 
 
+def test_noalloc_filter_full_array():
+    """g g > t t~ g g: 64 test events x 64 helicities, the most events the
+    fixed array takes, with the mask and count bit-exact against the
+    allocating filter on the same events, twice in a row."""
+    kw = dict(ptmin=20.0, drmin=0.4)
+    test = torch.from_numpy(ps.generate(64, 2, 1500.0, 4321, **kw)).cuda()
+    ref = binding.Process("g g > t t~ g g")
+    nref = ref.filter_helicities(test)
+    p = binding.Process("g g > t t~ g g")
+    for _ in range(2):
+        rc, n = _noalloc(p, test)
+        assert rc == binding.MG_OK and n == nref == 64
+        assert np.array_equal(p.helicity_mask(), ref.helicity_mask())
+
+
 def test_noalloc_filter_rejects_too_many_events():
     test = torch.from_numpy(ps.generate(65, 1, 1500.0, 5, ptmin=20.0, drmin=0.4)).cuda()
     p = binding.Process("g g > t t~ g")

@@ -391,10 +391,33 @@ def run_surrogate(args):
     torch.cuda.synchronize(dev)
     t_train = time.perf_counter() - t0
     assert rc == 0, rc
-    # calibration on the training slice
+    # calibration on the training slice (timed with CUDA events: inference
+    # throughput of the tensor-core MLP)
     pred_tr = torch.empty(ntrain, dtype=torch.float64, device=dev)
+    ia, ib = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ia.record(stream)
     L.mg_sur_predict(h, ctypes.c_void_p(trd.data_ptr()), 8, ntrain, ctypes.c_void_p(pred_tr.data_ptr()), sp)
+    ib.record(stream)
     torch.cuda.synchronize(dev)
+    t_infer = ia.elapsed_time(ib) / 1e3
+    # MLP work: tensor-core MMA flops as issued (K padded to 64-wide chunks,
+    # widths to 16) per row: forward sum_l 2 Kpad_l Npad_l; a training row
+    # adds the weight gradients (same) and the backward data GEMMs (l > 0)
+    sizes = [(32, 256), (256, 256), (256, 256), (256, 16)]
+    fwd_row = sum(2 * (-(-k // 64) * 64) * n for k, n in sizes)
+    bwd_row = fwd_row + sum(2 * n * k for k, n in sizes[1:])
+    train_flops = (ntrain // 4096) * 4096 * args.epochs * (fwd_row + bwd_row)
+    bf16 = _measured_peak("bf16_tflops")
+    mlp_roof = {"bound": "tensor", "unit": "TFLOP/s", "peak": bf16,
+                "kernel": "k_mlp_gemm (tcgen05; peak = measured cuBLAS bf16 burst)",
+                "train_achieved": train_flops / t_train / 1e12,
+                "train_frac": train_flops / t_train / 1e12 / bf16 if bf16 else None,
+                "train_step_ms": 1e3 * t_train / ((ntrain // 4096) * args.epochs),
+                "infer_achieved": ntrain * fwd_row / t_infer / 1e12,
+                "infer_frac": ntrain * fwd_row / t_infer / 1e12 / bf16 if bf16 else None,
+                "infer_events_per_s": ntrain / t_infer,
+                "note": "4096-row batches of a 32-256-256-256-1 network: about 30 launches per "
+                        "training step, launch and latency bound"}
     w_tr = me_tr.cpu().numpy() * phi_tr
     what_tr = np.exp(pred_tr.cpu().numpy()) * phi_tr
     what_max = float(np.quantile(what_tr, 0.999))
@@ -476,6 +499,7 @@ def run_surrogate(args):
             ntrain * p.info().ngood * (p.info().flops_diagram + p.info().flops_colour), t_exact,
             "k_sigmakin on the training events (wall time of the exact-ME pass)", _fp64_peak()),
         "training": {"seconds": t_train, "final_epoch_loss": loss.value, "r2_log_me_train": float(r2)},
+        "roofline_mlp": mlp_roof,
         "two_stage": {"what_max": what_max, "r_max": r_max, "runs": two_runs,
                       "ess_per_s": tw_m, "ess_per_s_err": tw_e},
         "plain_hit_or_miss": {"w_max_quantile": w_q, "exact_seconds": t_plain, "runs": plain_runs,

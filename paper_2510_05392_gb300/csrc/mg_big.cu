@@ -48,7 +48,7 @@ constexpr int BIG_BLOCK = 128;
 constexpr int CT = 64;   // colour tile (n and k) of the quadratic form
 constexpr int CK = 16;   // k chunk per shared-memory stage
 constexpr int RT = 64;   // rows per tile
-constexpr int SCAT_BATCH = 2;   // jamp updates loaded together
+constexpr int SCAT_BATCH = 4;   // jamp updates loaded together
 
 // slot-major, thread-interleaved state; p already offset by the thread
 struct Strided {

@@ -11,7 +11,8 @@
  * Schumann, Siegert, SciPost Phys. 12 (2022) 164), in which the exact matrix
  * element corrects every surrogate acceptance so the unweighted sample stays
  * exact:
- *   features  x = s_ij / s for all particle pairs i < j (s = s_12), padded
+ *   features  x = log(s_ij / s) for all particle pairs i < j (s = s_12),
+ *             padded
  *   network   nin -> hidden (x nhidden, SiLU) -> 1, BF16 weights and
  *             activations, FP32 accumulation, FP32 master weights, Adam
  *   target    y = (log|M|^2 - mu) / sigma, MSE loss

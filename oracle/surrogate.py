@@ -8,8 +8,11 @@ accepted ones"), following the published rejection-sampling scheme with
 network weight estimates (Danziger, Janssen, Schumann, Siegert, SciPost
 Phys. 12 (2022) 164):
 
-  features    x_k = s_ij / s for all particle pairs i < j (physical momenta,
-              s_ij = (p_i + p_j)^2, s = s_12), padded with zeros to nin
+  features    x_k = log(s_ij / s) for all particle pairs i < j (physical
+              momenta, s_ij = (p_i + p_j)^2 > 0, s = s_12), padded with zeros
+              to nin; the logarithm of the pair invariants is the network's
+              fixed input transform (|M|^2 varies as powers of the s_ij near
+              its poles, so log|M|^2 is close to linear in log s_ij)
   network     z_1 = W_1 x + b_1, a_l = silu(z_l), z_{l+1} = W_{l+1} a_l + b_{l+1},
               f = z_L (no activation on the output), silu(z) = z / (1 + e^-z)
   target      y = (log|M|^2 - mu) / sigma, mu and sigma over the training set
@@ -27,7 +30,7 @@ import numpy as np
 
 
 def features(mom: np.ndarray, nin: int = 32) -> np.ndarray:
-    """s_ij / s for i < j over the particles of mom [n][npar][4], zero padded."""
+    """log(s_ij / s) for i < j over the particles of mom [n][npar][4], zero padded."""
     n, npar, _ = mom.shape
     P = mom[:, 0] + mom[:, 1]
     s = P[:, 0] ** 2 - (P[:, 1:] ** 2).sum(1)
@@ -36,7 +39,7 @@ def features(mom: np.ndarray, nin: int = 32) -> np.ndarray:
     for i in range(npar):
         for j in range(i + 1, npar):
             q = mom[:, i] + mom[:, j]
-            out[:, k] = (q[:, 0] ** 2 - (q[:, 1:] ** 2).sum(1)) / s
+            out[:, k] = np.log((q[:, 0] ** 2 - (q[:, 1:] ** 2).sum(1)) / s)
             k += 1
     return out
 

@@ -3,7 +3,7 @@
 // The paper has no learned component; this is the benchmark configuration's
 // surrogate pattern, the published scheme of rejection sampling with network
 // weight estimates (Danziger, Janssen, Schumann, Siegert 2022):
-//   features  x = s_ij / s over all particle pairs (FP64, rounded to BF16)
+//   features  x = log(s_ij / s) over all particle pairs (FP64, rounded to BF16)
 //   network   z_1 = W_1 x + b_1, a = silu(z), ..., f = z_L;  sizes
 //             nin -> hidden (x nhidden, SiLU) -> 1; BF16 weights/activations,
 //             FP32 accumulation, FP32 master weights, Adam
@@ -39,9 +39,9 @@ constexpr int SUR_MAXL = 8;
 constexpr int WM = 16;     // padding of layer widths
 constexpr int MROWS = 128; // padding of batches (rows of one tensor-core tile)
 
-// features: x[e][k] = s_ij / s for pairs i < j (k in pair order), zero
-// padded, rows e >= n zero; written row-major [M][nin] and transposed
-// [nin][ldt]
+// features: x[e][k] = log(s_ij / s) for pairs i < j (k in pair order),
+// computed in FP64 and rounded to BF16, zero padded, rows e >= n zero;
+// written row-major [M][nin] and transposed [nin][ldt]
 __global__ void k_features(const double *__restrict__ mom, long long n, long long M, int npar, int nin,
                            __nv_bfloat16 *__restrict__ x, __nv_bfloat16 *__restrict__ xt, long long ldt) {
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -57,7 +57,7 @@ __global__ void k_features(const double *__restrict__ mom, long long n, long lon
                 const double q2 = p[4 * i + 2] + p[4 * j + 2], q3 = p[4 * i + 3] + p[4 * j + 3];
                 if (k < nin) {
                     const __nv_bfloat16 v =
-                        __float2bfloat16_rn((float)((q0 * q0 - q1 * q1 - q2 * q2 - q3 * q3) / s));
+                        __float2bfloat16_rn((float)log((q0 * q0 - q1 * q1 - q2 * q2 - q3 * q3) / s));
                     x[e * nin + k] = v;
                     xt[(long long)k * ldt + e] = v;
                 }

@@ -9,11 +9,16 @@ def test_features_are_pair_invariants():
     mom = ps.generate(50, 4, 2000.0, 3, ptmin=20.0, drmin=0.4)
     x = S.features(mom)
     assert x.shape == (50, 32)
-    np.testing.assert_allclose(x[:, 0], 1.0, rtol=1e-12)         # s_12 / s
+    np.testing.assert_allclose(x[:, 0], 0.0, atol=1e-12)         # log(s_12 / s)
     assert np.all(x[:, 28:] == 0.0)
     # massive pair (t, t~): s_34 >= 4 m^2
     k34 = [(i, j) for i in range(8) for j in range(i + 1, 8)].index((2, 3))
-    assert np.all(x[:, k34] * 2000.0 ** 2 >= 4 * 173.0 ** 2 * (1 - 1e-12))
+    assert np.all(np.exp(x[:, k34]) * 2000.0 ** 2 >= 4 * 173.0 ** 2 * (1 - 1e-12))
+    # an explicit pair: log((p_4 + p_6)^2 / s) from the four-vectors
+    k46 = [(i, j) for i in range(8) for j in range(i + 1, 8)].index((4, 6))
+    q = mom[:, 4] + mom[:, 6]
+    np.testing.assert_allclose(x[:, k46], np.log((q[:, 0] ** 2 - (q[:, 1:] ** 2).sum(1)) / 2000.0 ** 2),
+                               rtol=1e-9)
     # momentum conservation: sum over j != i of s_ij relates to masses, and
     # Lorentz invariance: a boost leaves the features unchanged
     b = np.array([0.3, -0.1, 0.4]); g = 1 / np.sqrt(1 - b @ b)

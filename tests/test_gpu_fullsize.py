@@ -72,3 +72,27 @@ def test_uneven_batch_full_size_sampled():
         assert np.all(np.isfinite(got)) and np.all(got > 0)
         idx = np.unique(np.linspace(0, len(m) - 1, 24).astype(np.int64))
         assert np.abs(got[idx] / oracle.me(m[idx]) - 1).max() <= RTOL["fp64"]
+
+
+@pytest.mark.parametrize("name", ["ggttgg_524288", "ggttggg_262144"])
+def test_mixed_against_fp64_every_event(name):
+    """The mixed-precision colour sum against the FP64 path (itself checked
+    against the oracle above) on every event of the full workload: the
+    per-process error bound of the mixed path is stated over the whole set,
+    not a sample."""
+    w = ps.WORKLOADS[name]
+    ng, sqrts = w["ngluon_final"], w["sqrts"]
+    md = torch.from_numpy(ps.workload(name)).cuda()
+    test = torch.from_numpy(ps.generate(16, ng, sqrts, 12345, ptmin=20.0, drmin=0.4)).cuda()
+    outs = []
+    for prec in (binding.MG_FP64, binding.MG_MIXED_BF16):
+        p = binding.Process("g g > t t~" + " g" * ng, precision=prec)
+        p.filter_helicities(test)
+        out = torch.empty(md.shape[0], dtype=torch.float64, device="cuda")
+        p.sigmakin(md, out)
+        assert p.device_status() == binding.MG_OK
+        outs.append(out)
+    rel = (outs[1] / outs[0] - 1).abs()
+    print(f"{name}: mixed vs FP64 over {md.shape[0]} events: max {rel.max().item():.3e}, "
+          f"median {rel.median().item():.3e}")
+    assert rel.max().item() <= RTOL["mixed"]

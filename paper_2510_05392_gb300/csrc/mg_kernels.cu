@@ -197,13 +197,21 @@ __device__ void write_jamp_rows(const cx (*J)[4], int mask, __nv_bfloat16 *__res
         for (int ri = 0; ri < 2; ri++) {
             __nv_bfloat16 *row = jout + (row0 + 2 * v + ri) * (long long)(3 * kp);
             for (int c0 = 0; c0 < kp; c0 += 8) {
+                if (!on || c0 >= NC) {  // padding colours, masked-out helicities: zeros
+                    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+                    *reinterpret_cast<uint4 *>(row + c0) = z;
+                    *reinterpret_cast<uint4 *>(row + kp + c0) = z;
+                    *reinterpret_cast<uint4 *>(row + 2 * kp + c0) = z;
+                    continue;
+                }
+                // only real colours pay for the FP64 -> FP32 conversion (an
+                // FP64-pipe instruction); the BF16 splitting runs in FP32
                 __align__(16) __nv_bfloat16 hi[8], mid[8], lo[8];
 #pragma unroll
                 for (int q = 0; q < 8; q++) {
                     const int c = c0 + q;
-                    double x = 0.0;
-                    if (on && c < NC) x = ri ? J[c][v].i : J[c][v].r;
-                    const float f = __double2float_rn(x);
+                    float f = 0.0f;
+                    if (c < NC) f = __double2float_rn(ri ? J[c][v].i : J[c][v].r);
                     hi[q] = __float2bfloat16_rn(f);
                     const float r1 = f - __bfloat162float(hi[q]);
                     mid[q] = __float2bfloat16_rn(r1);

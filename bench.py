@@ -416,8 +416,8 @@ def run_surrogate(args):
                 "infer_achieved": ntrain * fwd_row / t_infer / 1e12,
                 "infer_frac": ntrain * fwd_row / t_infer / 1e12 / bf16 if bf16 else None,
                 "infer_events_per_s": ntrain / t_infer,
-                "note": "4096-row batches of a 32-256-256-256-1 network: about 30 launches per "
-                        "training step, launch and latency bound"}
+                "note": "4096-row batches of a 32-256-256-256-1 network: one CUDA-graph launch "
+                        "of about 30 kernels per training step, latency bound"}
     w_tr = me_tr.cpu().numpy() * phi_tr
     what_tr = np.exp(pred_tr.cpu().numpy()) * phi_tr
     what_max = float(np.quantile(what_tr, 0.999))

@@ -26,6 +26,15 @@ int mg_probe_fp64_peak(int blocks, int iters, int reps, double *flops_out);
 struct mg_process;
 int mg_debug_inject_stall(struct mg_process *p, unsigned int extra_bytes);
 
+/* The same test hook for the surrogate's tensor-core GEMMs: every later GEMM
+ * launch of s makes its operand barrier expect extra_bytes more than its TMA
+ * copies deliver, so the MMA thread's bounded wait runs out (about a second
+ * per launch), the CTA records the timeout, frees its tensor memory and
+ * returns; mg_sur_device_status then reports MG_ERR_DEVICE_TIMEOUT.  0
+ * disables. */
+struct mg_surrogate;
+int mg_sur_debug_inject_stall(struct mg_surrogate *s, unsigned int extra_bytes);
+
 /* Kernel timing of one process.  mg_set_kernel_timing(p, n) with n > 0
  * creates n CUDA event pairs; every later mg_sigmakin or mg_sigmakin_hel
  * call on p then records a pair on the caller's stream around each of its

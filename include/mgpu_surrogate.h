@@ -64,9 +64,17 @@ int mg_sur_adam(mg_surrogate *s, double lr, void *stream);
  * *last_epoch_loss (host, may be NULL) = mean batch loss of the last epoch. */
 int mg_sur_train(mg_surrogate *s, const double *momenta_dev, int npar, const double *me_dev,
                  int64_t n, int epochs, int batch, double lr, void *stream, double *last_epoch_loss);
-/* Predicted log|M|^2 (= sigma f + mu) for n events into logme_dev[n]. */
+/* Predicted log|M|^2 (= sigma f + mu) for n events into logme_dev[n].
+ * Asynchronous; a bounded wait of its tensor-core GEMMs that gave up is
+ * reported by mg_sur_device_status or the next synchronising call. */
 int mg_sur_predict(mg_surrogate *s, const double *momenta_dev, int npar, int64_t n,
                    double *logme_dev, void *stream);
+/* Synchronises the stream; MG_ERR_DEVICE_TIMEOUT (and clears it) when a
+ * bounded wait inside one of the surrogate's tensor-core GEMMs gave up since
+ * the last check (its outputs are then not valid), MG_ERR_CUDA on a CUDA
+ * error, else MG_OK.  mg_sur_train, mg_sur_loss_grad with a loss output and
+ * mg_unweight2 make this check themselves. */
+int mg_sur_device_status(mg_surrogate *s, void *stream);
 
 /* Checkpoint / resume: weights, Adam state and target statistics in a
  * versioned binary file ("MGSUR001").  Load requires the same sizes. */

@@ -31,8 +31,9 @@ typedef struct {
 // (64-wide chunks, zero-filled past kdim and past the last row); D is M x N
 // (M multiple of 128, N multiple of nt, nt in 16..256 a multiple of 16);
 // ksplit slices of K (weight gradient only).  err: device word set to
-// MG_TC_ERR_TIMEOUT when a bounded wait gives up.
+// MG_TC_ERR_TIMEOUT when a bounded wait gives up.  extra_tx (test hook): bytes
+// the operand barrier expects beyond what arrives (0 in normal use).
 cudaError_t mg_launch_mlp_gemm(int mode, const __nv_bfloat16 *X, long long xrows, long long xld,
                                const __nv_bfloat16 *Y, long long yrows, long long yld, int kdim,
                                long long M, int N, int nt, int ksplit, const mg_mlp_epi &ep, int *err,
-                               cudaStream_t stream);
+                               cudaStream_t stream, uint32_t extra_tx = 0);

@@ -48,7 +48,8 @@ __device__ __forceinline__ float dsilu_f(float z) {
 template <int MODE>
 __global__ void __launch_bounds__(ML_THREADS, 1)
     k_mlp_gemm(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
-               int nt, int kchunks, int tmem_cols, mg_mlp_epi ep, int *__restrict__ err) {
+               int nt, int kchunks, int tmem_cols, uint32_t extra_tx, mg_mlp_epi ep,
+               int *__restrict__ err) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -93,7 +94,7 @@ __global__ void __launch_bounds__(ML_THREADS, 1)
                 break;
             }
             unsigned char *dst = smem + s * stage_bytes;
-            mbar_expect_tx(&full[s], (uint32_t)stage_bytes);
+            mbar_expect_tx(&full[s], (uint32_t)stage_bytes + extra_tx);
             tma_load_2d(dst, &tmX, (kc0 + c) * TC_KCHUNK, m0, &full[s]);
             tma_load_2d(dst + ML_X_BYTES, &tmY, (kc0 + c) * TC_KCHUNK, n0, &full[s]);
         }
@@ -136,48 +137,48 @@ __global__ void __launch_bounds__(ML_THREADS, 1)
             tmem_ld16(taddr + (uint32_t)c0, r);
             const int n = n0 + c0;
             if (m >= ep.m_valid) continue;
-            if (MODE == MG_MLP_WGRAD) {
+            if constexpr (MODE == MG_MLP_WGRAD) {
                 float *dst = ep.part + ((long long)blockIdx.z * ep.m_valid + m) * ep.ldz + n;
 #pragma unroll
                 for (int j = 0; j < 16; j++)
                     if (n + j < ep.n_valid) dst[j] = __uint_as_float(r[j]);
-                continue;
-            }
-            float v[16];
+            } else {
+                float v[16];
 #pragma unroll
-            for (int j = 0; j < 16; j++) v[j] = __uint_as_float(r[j]);
-            const long long o = (long long)m * ep.ldz + n;
-            if (MODE == MG_MLP_FWD || MODE == MG_MLP_FWD_OUT) {
+                for (int j = 0; j < 16; j++) v[j] = __uint_as_float(r[j]);
+                const long long o = (long long)m * ep.ldz + n;
+                if constexpr (MODE == MG_MLP_FWD || MODE == MG_MLP_FWD_OUT) {
 #pragma unroll
-                for (int j = 0; j < 16; j++) v[j] += __ldg(ep.bias + n + j);
+                    for (int j = 0; j < 16; j++) v[j] += __ldg(ep.bias + n + j);
 #pragma unroll
-                for (int q = 0; q < 4; q++)
-                    *reinterpret_cast<float4 *>(ep.Z + o + 4 * q) =
-                        make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-                if (MODE == MG_MLP_FWD) {
-                    __align__(16) __nv_bfloat16 a[16];
+                    for (int q = 0; q < 4; q++)
+                        *reinterpret_cast<float4 *>(ep.Z + o + 4 * q) =
+                            make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                    if constexpr (MODE == MG_MLP_FWD) {
+                        __align__(16) __nv_bfloat16 a[16];
 #pragma unroll
-                    for (int j = 0; j < 16; j++) a[j] = __float2bfloat16_rn(silu_f(v[j]));
-                    *reinterpret_cast<uint4 *>(ep.A + o) = *reinterpret_cast<const uint4 *>(a);
-                    *reinterpret_cast<uint4 *>(ep.A + o + 8) = *reinterpret_cast<const uint4 *>(a + 8);
+                        for (int j = 0; j < 16; j++) a[j] = __float2bfloat16_rn(silu_f(v[j]));
+                        *reinterpret_cast<uint4 *>(ep.A + o) = *reinterpret_cast<const uint4 *>(a);
+                        *reinterpret_cast<uint4 *>(ep.A + o + 8) = *reinterpret_cast<const uint4 *>(a + 8);
 #pragma unroll
-                    for (int j = 0; j < 16; j++) ep.AT[(long long)(n + j) * ep.ldt + m] = a[j];
+                        for (int j = 0; j < 16; j++) ep.AT[(long long)(n + j) * ep.ldt + m] = a[j];
+                    }
+                } else {  // MG_MLP_BWD_DATA
+                    __align__(16) __nv_bfloat16 d16[16];
+#pragma unroll
+                    for (int j = 0; j < 16; j++) {
+                        v[j] *= dsilu_f(__ldg(ep.Zprev + o + j));
+                        d16[j] = __float2bfloat16_rn(v[j]);
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; q++)
+                        *reinterpret_cast<float4 *>(ep.dZ32 + o + 4 * q) =
+                            make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                    *reinterpret_cast<uint4 *>(ep.dZ + o) = *reinterpret_cast<const uint4 *>(d16);
+                    *reinterpret_cast<uint4 *>(ep.dZ + o + 8) = *reinterpret_cast<const uint4 *>(d16 + 8);
+#pragma unroll
+                    for (int j = 0; j < 16; j++) ep.dZT[(long long)(n + j) * ep.ldt + m] = d16[j];
                 }
-            } else {  // MG_MLP_BWD_DATA
-                __align__(16) __nv_bfloat16 d16[16];
-#pragma unroll
-                for (int j = 0; j < 16; j++) {
-                    v[j] *= dsilu_f(__ldg(ep.Zprev + o + j));
-                    d16[j] = __float2bfloat16_rn(v[j]);
-                }
-#pragma unroll
-                for (int q = 0; q < 4; q++)
-                    *reinterpret_cast<float4 *>(ep.dZ32 + o + 4 * q) =
-                        make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-                *reinterpret_cast<uint4 *>(ep.dZ + o) = *reinterpret_cast<const uint4 *>(d16);
-                *reinterpret_cast<uint4 *>(ep.dZ + o + 8) = *reinterpret_cast<const uint4 *>(d16 + 8);
-#pragma unroll
-                for (int j = 0; j < 16; j++) ep.dZT[(long long)(n + j) * ep.ldt + m] = d16[j];
             }
         }
     }
@@ -213,7 +214,7 @@ bool make_map_ld(CUtensorMap *m, const void *base, uint64_t rows, uint64_t cols,
 cudaError_t mg_launch_mlp_gemm(int mode, const __nv_bfloat16 *X, long long xrows, long long xld,
                                const __nv_bfloat16 *Y, long long yrows, long long yld, int kdim,
                                long long M, int N, int nt, int ksplit, const mg_mlp_epi &ep, int *err,
-                               cudaStream_t stream) {
+                               cudaStream_t stream, uint32_t extra_tx) {
     // M rows of D in 128-row tiles, N columns in nt-column tiles, K = kdim
     // in 64-wide chunks, split in ksplit equal slices (weight gradient only);
     // TMA needs 16-byte row strides and a 16-byte aligned base
@@ -232,14 +233,24 @@ cudaError_t mg_launch_mlp_gemm(int mode, const __nv_bfloat16 *X, long long xrows
     while (tmem_cols < nt) tmem_cols <<= 1;
     const size_t smem = ml_smem_bytes(nt);
     const dim3 grid((unsigned)(M / TC_M), (unsigned)(N / nt), (unsigned)ksplit);
-    cudaError_t e = cudaSuccess;
+    // the dynamic shared-memory limit of each mode, raised once per device
+    // (a host call per launch would cost as much as the launch itself)
+    static size_t smem_set[64][4];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const bool raise = dev < 0 || dev >= 64 || mode < 0 || mode > 3 || smem_set[dev][mode] < smem;
     mg_note_launch();
     switch (mode) {
 #define ML_CASE(MD)                                                                                \
     case MD:                                                                                       \
-        e = cudaFuncSetAttribute(k_mlp_gemm<MD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-        if (e != cudaSuccess) return e;                                                            \
-        k_mlp_gemm<MD><<<grid, ML_THREADS, smem, stream>>>(mx, my, nt, kch / ksplit, tmem_cols, ep, err); \
+        if (raise) {                                                                               \
+            e = cudaFuncSetAttribute(k_mlp_gemm<MD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+            if (e != cudaSuccess) return e;                                                        \
+            if (dev >= 0 && dev < 64) smem_set[dev][MD] = smem;                                    \
+        }                                                                                          \
+        k_mlp_gemm<MD><<<grid, ML_THREADS, smem, stream>>>(mx, my, nt, kch / ksplit, tmem_cols, extra_tx, ep, \
+                                                           err);                                   \
         break;
         ML_CASE(MG_MLP_FWD)
         ML_CASE(MG_MLP_FWD_OUT)

@@ -43,9 +43,11 @@ constexpr int MROWS = 128; // padding of batches (rows of one tensor-core tile)
 // computed in FP64 and rounded to BF16, zero padded, rows e >= n zero;
 // written row-major [M][nin] and transposed [nin][ldt]
 __global__ void k_features(const double *__restrict__ mom, long long n, long long M, int npar, int nin,
-                           __nv_bfloat16 *__restrict__ x, __nv_bfloat16 *__restrict__ xt, long long ldt) {
+                           __nv_bfloat16 *__restrict__ x, __nv_bfloat16 *__restrict__ xt, long long ldt,
+                           const int *__restrict__ bidx = nullptr) {
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= M) return;
+    if (bidx) mom += (long long)(*bidx) * n * npar * 4;   // batch *bidx of n rows
     int k = 0;
     if (e < n) {
         const double *p = mom + e * npar * 4;
@@ -140,9 +142,15 @@ __global__ void k_loss(const float *__restrict__ Zout, long long M, int nvalid, 
 __global__ void k_adam(float *__restrict__ p, float *__restrict__ m, float *__restrict__ v,
                        const float *__restrict__ g, __nv_bfloat16 *__restrict__ p16,
                        __nv_bfloat16 *__restrict__ p16t, int rows, int cols, float lr, float b1,
-                       float b2, float eps, float c1, float c2) {
+                       float b2, float eps, float c1, float c2,
+                       const int *__restrict__ steps = nullptr) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (long long)rows * cols) return;
+    if (steps) {  // bias corrections of step *steps + 1, from the device-side step count
+        const float t = (float)(*steps + 1);
+        c1 = 1.0f - powf(b1, t);
+        c2 = 1.0f - powf(b2, t);
+    }
     const float gi = g[i];
     const float mi = b1 * m[i] + (1.0f - b1) * gi;
     const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
@@ -154,11 +162,27 @@ __global__ void k_adam(float *__restrict__ p, float *__restrict__ m, float *__re
     if (p16t) p16t[(i % cols) * rows + i / cols] = __float2bfloat16_rn(w);
 }
 
-// target: y = (log me - mu) / sigma, with mu/sigma from k_logstats
+// target: y = (log me - mu) / sigma, with mu/sigma from k_logstats (of
+// batch *bidx of n rows when bidx is given)
 __global__ void k_target(const double *__restrict__ me, long long n, const double *__restrict__ ms,
-                         float *__restrict__ y) {
+                         float *__restrict__ y, const int *__restrict__ bidx = nullptr) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (bidx) me += (long long)(*bidx) * n;
     if (i < n) y[i] = (float)((log(me[i]) - ms[0]) / ms[1]);
+}
+
+// device-side training state: [0] batch index within the epoch, [1] Adam
+// steps taken; advanced once per training step
+__global__ void k_step_advance(int *__restrict__ st) {
+    st[0] += 1;
+    st[1] += 1;
+}
+
+// acc += sum of a batch's loss partial sums, in a fixed order
+__global__ void k_loss_acc(const double *__restrict__ part, int nb, double *__restrict__ acc) {
+    double t = 0.0;
+    for (int b = 0; b < nb; b++) t += part[b];
+    acc[0] += t;
 }
 
 // mean and standard deviation of log(me) (single block, fixed order)
@@ -290,6 +314,10 @@ struct mg_surrogate {
     double *part;                // loss partial sums
     float *y;                    // standardised targets of a chunk
     int *err;                    // device error word of the bounded waits
+    uint32_t debug_extra_tx;     // test hook: extra bytes the GEMMs' operand barrier expects
+    int *dstate;                 // device training state (k_step_advance)
+    double *dloss;               // device sum of batch losses of an epoch
+    cudaStream_t cap;            // private stream the training step is captured on
 };
 
 namespace {
@@ -315,6 +343,8 @@ void free_sur(mg_surrogate *s) {
         cudaFree(s->AT[l]);
     }
     cudaFree(s->wpart); cudaFree(s->ms); cudaFree(s->part); cudaFree(s->y); cudaFree(s->err);
+    cudaFree(s->dstate); cudaFree(s->dloss);
+    if (s->cap) cudaStreamDestroy(s->cap);
     delete s;
 }
 
@@ -351,7 +381,7 @@ int forward(mg_surrogate *s, long long M, cudaStream_t st) {
         ep.n_valid = s->outp[l];
         SCHECK(mg_launch_mlp_gemm(last ? MG_MLP_FWD_OUT : MG_MLP_FWD, s->A[l], M, s->in[l], s->W16[l],
                                   s->outp[l], s->in[l], s->in[l], M, s->outp[l], pick_nt(s->outp[l]), 1,
-                                  ep, s->err, st));
+                                  ep, s->err, st, s->debug_extra_tx));
     }
     return MG_OK;
 }
@@ -369,7 +399,7 @@ int backward(mg_surrogate *s, long long M, cudaStream_t st) {
         // gW[n][k] = sum_m dZ[m][n] A[m][k]: X = dZ^T [outp][batch], Y = A^T [in][batch]
         SCHECK(mg_launch_mlp_gemm(MG_MLP_WGRAD, s->dZT[l], s->outp[l], s->bmax, s->AT[l], s->in[l],
                                   s->bmax, (int)M, pad_rows(s->outp[l]), s->in[l], pick_nt(s->in[l]), ns,
-                                  ep, s->err, st));
+                                  ep, s->err, st, s->debug_extra_tx));
         const long long nw = (long long)s->outp[l] * s->in[l];
         mg_note_launch();
         k_wgrad_reduce<<<blocks_for(nw, 256), 256, 0, st>>>(s->wpart, ns, nw, s->gW[l]);
@@ -389,7 +419,7 @@ int backward(mg_surrogate *s, long long M, cudaStream_t st) {
             ed.n_valid = s->in[l];
             SCHECK(mg_launch_mlp_gemm(MG_MLP_BWD_DATA, s->dZ[l], M, s->outp[l], s->WT16[l], s->in[l],
                                       s->outp[l], s->outp[l], M, s->in[l], pick_nt(s->in[l]), 1, ed,
-                                      s->err, st));
+                                      s->err, st, s->debug_extra_tx));
         }
     }
     SCHECK(cudaGetLastError());
@@ -487,6 +517,9 @@ int mg_sur_create(int nin, int hidden, int nhidden, uint64_t seed, int bmax, mg_
         if (e == cudaSuccess) e = cudaMalloc(&s->y, (size_t)bmax * sizeof(float));
         if (e == cudaSuccess) e = cudaMalloc(&s->err, sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(s->err, 0, sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&s->dstate, 2 * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&s->dloss, sizeof(double));
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking);
         const double ms0[2] = {0.0, 1.0};
         if (e == cudaSuccess) e = cudaMemcpy(s->ms, ms0, sizeof(ms0), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) rc = sur_fail(e);
@@ -636,33 +669,114 @@ int mg_sur_adam(mg_surrogate *s, double lr, void *stream) {
     return MG_OK;
 }
 
+// One training step on batch dstate[0] of `batch` rows of mom / me (device-
+// side batch index and Adam step count, so the same launches serve every
+// step): targets, features, forward, loss (added to dloss), backward, Adam,
+// advance of the device state.
+static int train_step(mg_surrogate *s, const double *mom, int npar, const double *me, int batch,
+                      double lr, cudaStream_t st) {
+    const long long M = pad_rows(batch);
+    mg_note_launch();
+    k_target<<<blocks_for(batch, 256), 256, 0, st>>>(me, batch, s->ms, s->y, s->dstate);
+    mg_note_launch();
+    k_features<<<blocks_for(M, 128), 128, 0, st>>>(mom, batch, M, npar, s->in[0], s->A[0], s->AT[0], s->bmax,
+                                                  s->dstate);
+    int rc = forward(s, M, st);
+    if (rc) return rc;
+    const int nb = blocks_for(M, 256);
+    mg_note_launch();
+    k_loss<<<nb, 256, 0, st>>>(s->Z[s->nl - 1], M, batch, s->outp[s->nl - 1], s->y, s->dZ[s->nl - 1],
+                               s->dZT[s->nl - 1], s->bmax, s->dZ32[s->nl - 1], s->part);
+    mg_note_launch();
+    k_loss_acc<<<1, 1, 0, st>>>(s->part, nb, s->dloss);
+    rc = backward(s, M, st);
+    if (rc) return rc;
+    const float b1 = 0.9f, b2 = 0.999f;
+    for (int l = 0; l < s->nl; l++) {
+        const long long nw = (long long)s->outp[l] * s->in[l];
+        mg_note_launch();
+        k_adam<<<blocks_for(nw, 256), 256, 0, st>>>(s->W[l], s->mW[l], s->vW[l], s->gW[l], s->W16[l],
+                                                   s->WT16[l], s->outp[l], s->in[l], (float)lr, b1, b2,
+                                                   1e-8f, 1.0f, 1.0f, s->dstate + 1);
+        mg_note_launch();
+        k_adam<<<blocks_for(s->outp[l], 256), 256, 0, st>>>(s->b[l], s->mb[l], s->vb[l], s->gb[l], nullptr,
+                                                           nullptr, 1, s->outp[l], (float)lr, b1, b2,
+                                                           1e-8f, 1.0f, 1.0f, s->dstate + 1);
+    }
+    mg_note_launch();
+    k_step_advance<<<1, 1, 0, st>>>(s->dstate);
+    SCHECK(cudaGetLastError());
+    return MG_OK;
+}
+
 // Training: targets from me_dev (standardised with mg_sur_fit_target's mu,
 // sigma), full batches in data order, `epochs` passes, Adam after each batch.
+// The first step runs as plain launches; the step is then captured once as a
+// CUDA graph (on the surrogate's private stream; it reads the batch index and
+// the Adam step from device memory) and replayed for every later step on the
+// caller's stream, so a step costs one graph launch instead of about thirty.
 int mg_sur_train(mg_surrogate *s, const double *mom, int npar, const double *me, int64_t n,
                  int epochs, int batch, double lr, void *stream, double *last_epoch_loss) {
-    if (!s || !mom || !me || batch < 16 || batch % 16 || batch > s->bmax || n < batch || epochs < 1)
+    if (!s || !mom || !me || batch < 16 || batch % 16 || batch > s->bmax || n < batch || epochs < 1 ||
+        !(lr > 0))
         return MG_ERR_BAD_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t nbatch = n / batch;
-    double acc = 0.0;
-    for (int ep = 0; ep < epochs; ep++) {
-        acc = 0.0;
-        for (int64_t bi = 0; bi < nbatch; bi++) {
-            const double *mb = mom + (size_t)bi * batch * npar * 4;
-            mg_note_launch();
-            k_target<<<blocks_for(batch, 256), 256, 0, st>>>(me + bi * batch, batch, s->ms, s->y);
-            double l = 0.0;
-            int rc = mg_sur_loss_grad(s, mb, npar, s->y, batch, ep == epochs - 1 ? &l : nullptr, st);
-            if (rc) return rc;
-            acc += l;
-            rc = mg_sur_adam(s, lr, st);
-            if (rc) return rc;
+    int h0[2] = {0, s->t};   // pageable source: copied before the call returns
+    SCHECK(cudaMemcpyAsync(s->dstate, h0, sizeof(h0), cudaMemcpyHostToDevice, st));
+    SCHECK(cudaMemsetAsync(s->dloss, 0, sizeof(double), st));
+    cudaGraphExec_t exec = nullptr;
+    int rc = MG_OK;
+    for (int ep = 0; ep < epochs && !rc; ep++) {
+        cudaError_t e = cudaMemsetAsync(s->dstate, 0, sizeof(int), st);   // batch index 0
+        if (e == cudaSuccess && ep == epochs - 1) e = cudaMemsetAsync(s->dloss, 0, sizeof(double), st);
+        if (e != cudaSuccess) {
+            rc = sur_fail(e);
+            break;
+        }
+        for (int64_t bi = 0; bi < nbatch && !rc; bi++) {
+            if (exec) {
+                e = cudaGraphLaunch(exec, st);
+                if (e != cudaSuccess) rc = sur_fail(e);
+                continue;
+            }
+            rc = train_step(s, mom, npar, me, batch, lr, st);
+            if (rc || ep * nbatch + bi + 1 == epochs * nbatch) continue;
+            // capture the step once (nothing runs during capture)
+            cudaGraph_t graph = nullptr;
+            e = cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                const int rs = train_step(s, mom, npar, me, batch, lr, s->cap);
+                e = cudaStreamEndCapture(s->cap, &graph);
+                if (rs) rc = rs;
+            }
+            if (!rc && e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (!rc && e != cudaSuccess) rc = sur_fail(e);
         }
     }
-    const int rc = device_status(s, st);
+    if (exec) cudaGraphExecDestroy(exec);
+    double hloss = 0.0;
+    if (!rc) {
+        const cudaError_t e = cudaMemcpyAsync(&hloss, s->dloss, sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) rc = sur_fail(e);
+    }
+    if (!rc) rc = device_status(s, st);   // synchronises the stream
     if (rc) return rc;
-    if (last_epoch_loss) *last_epoch_loss = acc / (double)nbatch;
+    s->t += (int)(epochs * nbatch);
+    if (last_epoch_loss) *last_epoch_loss = hloss / ((double)nbatch * batch);
     return MG_OK;
+}
+
+int mg_sur_debug_inject_stall(mg_surrogate *s, unsigned int extra_bytes) {
+    if (!s) return MG_ERR_BAD_ARG;
+    s->debug_extra_tx = extra_bytes;
+    return MG_OK;
+}
+
+int mg_sur_device_status(mg_surrogate *s, void *stream) {
+    if (!s) return MG_ERR_BAD_ARG;
+    return device_status(s, (cudaStream_t)stream);
 }
 
 // Prediction of log|M|^2 for n events (chunks of bmax rows; n arbitrary).
@@ -807,6 +921,7 @@ int mg_unweight2(mg_process *p, mg_surrogate *s, const double *mom, const double
         e = cudaStreamSynchronize(st);
         if (!rc && e != cudaSuccess) rc = sur_fail(e);
     }
+    if (!rc) rc = device_status(s, st);   // a bounded wait of the surrogate's GEMMs gave up
     cudaFree(logme); cudaFree(what); cudaFree(flag); cudaFree(bcount); cudaFree(total);
     cudaFree(idx); cudaFree(mom1); cudaFree(me1);
     if (!rc && n_exact) *n_exact = htotal;

@@ -32,6 +32,7 @@ def _lib():
         "mg_sur_get_grads": ([vp, fp], ctypes.c_int),
         "mg_sur_loss_grad": ([vp, vp, ctypes.c_int, vp, ctypes.c_int, dp, vp], ctypes.c_int),
         "mg_sur_fit_target": ([vp, vp, ctypes.c_int64, vp], ctypes.c_int),
+        "mg_sur_adam": ([vp, ctypes.c_double, vp], ctypes.c_int),
         "mg_sur_get_target_stats": ([vp, dp], ctypes.c_int),
         "mg_sur_train": ([vp, vp, ctypes.c_int, vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                           ctypes.c_double, vp, dp], ctypes.c_int),
@@ -276,3 +277,70 @@ def test_two_stage_unweighting_exact_and_gain():
     print(f"effective unweighted events per exact ME: plain {plain:.4f}, two-stage {two:.4f}, "
           f"gain {two / plain:.2f} (accepted {keep.sum()} / {acc_g.sum()})")
     assert two > 2 * plain
+
+
+def test_bounded_wait_reports_timeout_and_context_stays_usable():
+    """The tensor-core GEMMs' mbarrier waits are bounded: with the test hook
+    making the operand barrier expect more bytes than its TMA copies deliver,
+    every GEMM gives up after about a second, records the timeout and returns;
+    mg_sur_device_status reports it once, and the next prediction on the same
+    context is bit-identical to one made before the stall."""
+    L = _lib()
+    L.mg_sur_debug_inject_stall.argtypes = [ctypes.c_void_p, ctypes.c_uint]
+    L.mg_sur_device_status.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    h = _new(L, bmax=256)
+    s = _stream()
+    md = torch.from_numpy(ps.generate(128, 2, 1500.0, 81, ptmin=20.0, drmin=0.4)).cuda()
+    ref = torch.empty(128, dtype=torch.float64, device="cuda")
+    assert L.mg_sur_predict(h, ctypes.c_void_p(md.data_ptr()), 6, 128, ctypes.c_void_p(ref.data_ptr()), s) == 0
+    assert L.mg_sur_device_status(h, s) == binding.MG_OK
+    assert L.mg_sur_debug_inject_stall(h, 16) == 0
+    out = torch.empty_like(ref)
+    assert L.mg_sur_predict(h, ctypes.c_void_p(md.data_ptr()), 6, 128, ctypes.c_void_p(out.data_ptr()), s) == 0
+    assert L.mg_sur_device_status(h, s) == binding.MG_ERR_DEVICE_TIMEOUT
+    assert L.mg_sur_device_status(h, s) == binding.MG_OK        # reported once
+    assert L.mg_sur_debug_inject_stall(h, 0) == 0
+    assert L.mg_sur_predict(h, ctypes.c_void_p(md.data_ptr()), 6, 128, ctypes.c_void_p(out.data_ptr()), s) == 0
+    assert L.mg_sur_device_status(h, s) == binding.MG_OK
+    assert torch.equal(out, ref)
+    L.mg_sur_destroy(h)
+
+
+def test_graph_replayed_training_matches_plain_steps():
+    """mg_sur_train replays one captured training step as a CUDA graph (device-
+    side batch index and Adam step count); the same batches run as explicit
+    mg_sur_loss_grad + mg_sur_adam calls on an identical network give the
+    same parameters and last-epoch loss (the bias corrections are computed on
+    the device in one path and on the host in the other, hence a tolerance)."""
+    L = _lib()
+    p, mom, md, me = _train_set(1, 8192, 95)
+    s = _stream()
+    ha, hb = _new(L, seed=21), _new(L, seed=21)
+    for h in (ha, hb):
+        assert L.mg_sur_fit_target(h, ctypes.c_void_p(me.data_ptr()), 8192, s) == 0
+    la = ctypes.c_double()
+    assert L.mg_sur_train(ha, ctypes.c_void_p(md.data_ptr()), 5, ctypes.c_void_p(me.data_ptr()), 8192, 3,
+                          4096, 1e-3, s, ctypes.byref(la)) == 0
+    ms = (ctypes.c_double * 2)()
+    L.mg_sur_get_target_stats(hb, ms)
+    y = ((torch.log(me) - ms[0]) / ms[1]).float()
+    lb = []
+    for ep in range(3):
+        for b in range(2):
+            l = ctypes.c_double()
+            assert L.mg_sur_loss_grad(hb, ctypes.c_void_p(md[4096 * b:].data_ptr()), 5,
+                                      ctypes.c_void_p(y[4096 * b:].data_ptr()), 4096, ctypes.byref(l), s) == 0
+            assert L.mg_sur_adam(hb, 1e-3, s) == 0
+            if ep == 2:
+                lb.append(l.value)
+    torch.cuda.synchronize()
+    n = ctypes.c_int64()
+    L.mg_sur_param_count(ha, ctypes.byref(n))
+    pa, pb = np.zeros(n.value, np.float32), np.zeros(n.value, np.float32)
+    L.mg_sur_get_params(ha, pa.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+    L.mg_sur_get_params(hb, pb.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+    print(f"graph vs plain steps: max |dp| {np.abs(pa - pb).max():.2e}, loss {la.value:.6f} / {np.mean(lb):.6f}")
+    assert np.abs(pa - pb).max() <= 1e-4 * np.abs(pb).max()
+    assert abs(la.value / np.mean(lb) - 1) < 1e-4
+    L.mg_sur_destroy(ha)
+    L.mg_sur_destroy(hb)

@@ -39,9 +39,11 @@ constexpr int SUR_MAXL = 8;
 constexpr int WM = 16;     // padding of layer widths
 constexpr int MROWS = 128; // padding of batches (rows of one tensor-core tile)
 
-// features: x[e][k] = log(s_ij / s) for pairs i < j (k in pair order),
-// computed in FP64 and rounded to BF16, zero padded, rows e >= n zero;
-// written row-major [M][nin] and transposed [nin][ldt]
+// features: x[e][k] = log(s_ij / s) for pairs i < j (k in pair order): the
+// ratio in FP64, its logarithm in FP32 (a BF16 input needs 8 bits; an FP64
+// logarithm would cost ~40 instructions of the slow FP64 pipe per pair),
+// rounded to BF16; zero padded, rows e >= n zero; written row-major [M][nin]
+// and transposed [nin][ldt]
 __global__ void k_features(const double *__restrict__ mom, long long n, long long M, int npar, int nin,
                            __nv_bfloat16 *__restrict__ x, __nv_bfloat16 *__restrict__ xt, long long ldt,
                            const int *__restrict__ bidx = nullptr) {
@@ -59,7 +61,7 @@ __global__ void k_features(const double *__restrict__ mom, long long n, long lon
                 const double q2 = p[4 * i + 2] + p[4 * j + 2], q3 = p[4 * i + 3] + p[4 * j + 3];
                 if (k < nin) {
                     const __nv_bfloat16 v =
-                        __float2bfloat16_rn((float)log((q0 * q0 - q1 * q1 - q2 * q2 - q3 * q3) / s));
+                        __float2bfloat16_rn(logf((float)((q0 * q0 - q1 * q1 - q2 * q2 - q3 * q3) / s)));
                     x[e * nin + k] = v;
                     xt[(long long)k * ldt + e] = v;
                 }
@@ -72,33 +74,46 @@ __global__ void k_features(const double *__restrict__ mom, long long n, long lon
     }
 }
 
-// gW[i] = sum over the splits of the weight-gradient partials, fixed order
-__global__ void k_wgrad_reduce(const float *__restrict__ part, int nsplit, long long n,
-                               float *__restrict__ gW) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    float s = 0.0f;
-    for (int k = 0; k < nsplit; k++) s += part[(long long)k * n + i];
-    gW[i] = s;
-}
-
-// gb[n] = sum_m dZ[m][n] from the FP32 values (the BF16 copies feed the
-// weight-gradient GEMM; their rounding would not cancel in this sum): 32
-// columns per block, 8 row slices per column summed in FP64 and added in a
-// fixed order
-__global__ void k_bias_grad(const float *__restrict__ dZ, long long M, int N, float *__restrict__ gb) {
+// Bias gradient gb[n] = sum_m dZ[m][n] from the FP32 values (the BF16 copies
+// feed the weight-gradient GEMM; their rounding would not cancel in this
+// sum), in two fixed-order levels: k_bias_part sums 128-row chunks (block:
+// 32 columns x 8 row slices of 16 rows, FP64), k_wgrad_reduce adds the chunks.
+constexpr int BIAS_ROWS = 128;
+__global__ void k_bias_part(const float *__restrict__ dZ, long long M, int N, double *__restrict__ bpart) {
     __shared__ double red[8][32];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int n = blockIdx.x * 32 + tx;
+    const long long m0 = (long long)blockIdx.y * BIAS_ROWS;
     double s = 0.0;
-    if (n < N)
-        for (long long m = ty; m < M; m += 8) s += dZ[m * N + n];
+    if (n < N) {
+#pragma unroll
+        for (int r = ty; r < BIAS_ROWS; r += 8)
+            if (m0 + r < M) s += dZ[(m0 + r) * N + n];
+    }
     red[ty][tx] = s;
     __syncthreads();
     if (ty == 0 && n < N) {
         double t = 0.0;
         for (int k = 0; k < 8; k++) t += red[k][tx];
-        gb[n] = (float)t;
+        bpart[(long long)blockIdx.y * N + n] = t;
+    }
+}
+
+// gW[i] = sum over the splits of the weight-gradient partials, and (i < nb)
+// gb[i] = sum over the row chunks of the bias partials, both in a fixed order
+__global__ void k_wgrad_reduce(const float *__restrict__ part, int nsplit, long long n,
+                               float *__restrict__ gW, const double *__restrict__ bpart, int nchunk,
+                               int nb, float *__restrict__ gb) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        float s = 0.0f;
+        for (int k = 0; k < nsplit; k++) s += part[(long long)k * n + i];
+        gW[i] = s;
+    }
+    if (i < nb) {
+        double t = 0.0;
+        for (int k = 0; k < nchunk; k++) t += bpart[(long long)k * nb + i];
+        gb[i] = (float)t;
     }
 }
 
@@ -315,6 +330,7 @@ struct mg_surrogate {
     float *y;                    // standardised targets of a chunk
     int *err;                    // device error word of the bounded waits
     uint32_t debug_extra_tx;     // test hook: extra bytes the GEMMs' operand barrier expects
+    double *bpart;               // bias-gradient partials [bmax / 128][outp]
     int *dstate;                 // device training state (k_step_advance)
     double *dloss;               // device sum of batch losses of an epoch
     cudaStream_t cap;            // private stream the training step is captured on
@@ -343,7 +359,7 @@ void free_sur(mg_surrogate *s) {
         cudaFree(s->AT[l]);
     }
     cudaFree(s->wpart); cudaFree(s->ms); cudaFree(s->part); cudaFree(s->y); cudaFree(s->err);
-    cudaFree(s->dstate); cudaFree(s->dloss);
+    cudaFree(s->dstate); cudaFree(s->dloss); cudaFree(s->bpart);
     if (s->cap) cudaStreamDestroy(s->cap);
     delete s;
 }
@@ -401,10 +417,13 @@ int backward(mg_surrogate *s, long long M, cudaStream_t st) {
                                   s->bmax, (int)M, pad_rows(s->outp[l]), s->in[l], pick_nt(s->in[l]), ns,
                                   ep, s->err, st, s->debug_extra_tx));
         const long long nw = (long long)s->outp[l] * s->in[l];
+        const int nchunk = (int)((M + BIAS_ROWS - 1) / BIAS_ROWS);
         mg_note_launch();
-        k_wgrad_reduce<<<blocks_for(nw, 256), 256, 0, st>>>(s->wpart, ns, nw, s->gW[l]);
+        k_bias_part<<<dim3((unsigned)blocks_for(s->outp[l], 32), (unsigned)nchunk), 256, 0, st>>>(
+            s->dZ32[l], M, s->outp[l], s->bpart);
         mg_note_launch();
-        k_bias_grad<<<blocks_for(s->outp[l], 32), 256, 0, st>>>(s->dZ32[l], M, s->outp[l], s->gb[l]);
+        k_wgrad_reduce<<<blocks_for(nw, 256), 256, 0, st>>>(s->wpart, ns, nw, s->gW[l], s->bpart, nchunk,
+                                                           s->outp[l], s->gb[l]);
         if (l > 0) {
             // dZ_l-1 = (dZ_l W_l) * silu'(Z_l-1): X = dZ_l [batch][outp], Y = W_l^T [in][outp]
             mg_mlp_epi ed;
@@ -518,6 +537,9 @@ int mg_sur_create(int nin, int hidden, int nhidden, uint64_t seed, int bmax, mg_
         if (e == cudaSuccess) e = cudaMalloc(&s->err, sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(s->err, 0, sizeof(int));
         if (e == cudaSuccess) e = cudaMalloc(&s->dstate, 2 * sizeof(int));
+        int omax = 0;
+        for (int l = 0; l < s->nl; l++) omax = s->outp[l] > omax ? s->outp[l] : omax;
+        if (e == cudaSuccess) e = cudaMalloc(&s->bpart, (size_t)(bmax / BIAS_ROWS) * omax * sizeof(double));
         if (e == cudaSuccess) e = cudaMalloc(&s->dloss, sizeof(double));
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking);
         const double ms0[2] = {0.0, 1.0};

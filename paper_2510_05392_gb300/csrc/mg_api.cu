@@ -151,8 +151,8 @@ int set_hel_list(mg_process *p, const uint8_t *mask, bool async = false, cudaStr
 int setup_mixed(mg_process *p) {
     const mg_proc_table *t = p->tab;
     const int nc = t->ncolor;
-    if (nc <= 128) {   // one tile holds every colour flow
-        p->kp = 64 * ((nc + 63) / 64);
+    if (nc <= 128) {   // one tile holds every colour flow (32-colour rows up to 32 flows)
+        p->kp = nc <= 32 ? 32 : 64 * ((nc + 63) / 64);
         p->np = 16 * ((nc + 15) / 16);
     } else {           // block upper triangle in 128-colour blocks
         p->kp = 128 * ((nc + 127) / 128);

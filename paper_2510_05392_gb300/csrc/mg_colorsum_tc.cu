@@ -37,10 +37,11 @@ using namespace mgtc;
 
 // Warp-specialised persistent kernel (2 + 8 TC_NSPLIT warps):
 //   warp 0  TMA producer: the two colour-matrix halves once, then the A chunks
-//           (one split x 64 colours x 128 rows, 16 KiB) of every tile through
+//           (one split x KW colours x 128 rows: 16 KiB at KW = 64, 8 KiB at
+//           KW = 32 for up to 32 flows) of every tile through
 //           a ring of TC_STAGES shared-memory stages (full/empty mbarriers);
-//   warp 1  MMA issuer (one thread): per chunk 4 (hi) or 8 (hi + lo colour
-//           matrix) tcgen05.mma, then tcgen05.commit to the stage's "empty"
+//   warp 1  MMA issuer (one thread): per chunk KW / 16 (hi) or KW / 8 (hi +
+//           lo colour matrix) tcgen05.mma, then tcgen05.commit to the stage's "empty"
 //           barrier; per tile a commit to the accumulator's "full" barrier;
 //           two TMEM accumulators alternate between the CTA's tiles;
 //   warps 2.. epilogue, two groups: group a takes the CTA's tiles i with
@@ -51,7 +52,8 @@ using namespace mgtc;
 //           16-colour groups g with g % TC_NSPLIT equal to its set.  A thread
 //           reads its row's colours from every A chunk in the stage the MMAs
 //           read (128-byte swizzle: 16-byte piece j of row m sits at piece
-//           j ^ (m % 8), so a warp's reads are conflict-free) and sums
+//           j ^ (m % 8); 64-byte swizzle: at j ^ ((m / 2) % 4); a warp's
+//           reads are conflict-free either way) and sums
 //           V = hi + mid + lo in registers; a stage is free once the MMA
 //           commit and the 4 TC_NSPLIT warps of the tile's group have
 //           arrived.  After the accumulator lands the thread forms its part of
@@ -88,8 +90,11 @@ __device__ __forceinline__ void tc_fail(int *failed, int *err) {
     atomicExch(err, MG_TC_ERR_TIMEOUT);
 }
 
-// KCN = kp / 64 colour chunks per split (1 for up to 64 colours, 2 for up to 128).
-template <int KCN>
+// KW colours per chunk (64: 128-byte rows and swizzle; 32: 64-byte rows and
+// swizzle, for up to 32 flows, so 24 flows read 1.33x their bytes instead of
+// 2.67x); KCN = kp / KW colour chunks per split (1 for up to KW colours, 2 for
+// up to 128).
+template <int KW, int KCN>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_colorsum_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                   int np, int np_pad, int cpe, long long ntiles, int tmem_cols, uint32_t extra_tx,
@@ -98,10 +103,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     constexpr int kc_n = KCN;
-    constexpr int kp = KCN * TC_KCHUNK;
+    constexpr int kp = KCN * KW;
     constexpr int nchunk = 3 * KCN;             // A chunks per tile: split-major
-    const int a_chunk = TC_M * 128;
-    const int b_chunk = np * 128;
+    constexpr int RB = 2 * KW;                  // bytes per row of a chunk
+    constexpr int GPC = KW / 16;                // 16-colour groups per chunk
+    static_assert((KW == 32 || KW == TC_KCHUNK) && GPC % TC_NSPLIT == 0, "chunk width");
+    const int a_chunk = TC_M * RB;
+    const int b_chunk = np * RB;
     unsigned char *sB = smem;                   // [2][kc_n] chunks, resident
     unsigned char *sA = sB + 2 * kc_n * b_chunk;  // [TC_STAGES] chunks
     uint64_t *bars = reinterpret_cast<uint64_t *>(sA + TC_STAGES * a_chunk);
@@ -145,7 +153,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_expect_tx(S.bB, (uint32_t)(2 * kc_n * b_chunk));
             for (int h = 0; h < 2; h++)
                 for (int kc = 0; kc < kc_n; kc++)
-                    tma_load_2d(sB + (h * kc_n + kc) * b_chunk, &tmB, kc * TC_KCHUNK, h * np, S.bB);
+                    tma_load_2d(sB + (h * kc_n + kc) * b_chunk, &tmB, kc * KW, h * np, S.bB);
             long long q[TC_NGROUP] = {0, 0};   // fills per ring
             int k = 0;                          // tile index among this CTA's tiles
             for (long long t = blockIdx.x; t < ntiles && !*(volatile int *)S.failed; t += gridDim.x, k++) {
@@ -160,7 +168,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     }
                     mbar_expect_tx(&S.full[stage], (uint32_t)a_chunk + extra_tx);
                     const int sp = c / kc_n, kc = c % kc_n;
-                    tma_load_2d(sA + stage * a_chunk, &tmA, sp * kp + kc * TC_KCHUNK, (int)(t * TC_M),
+                    tma_load_2d(sA + stage * a_chunk, &tmA, sp * kp + kc * KW, (int)(t * TC_M),
                                 &S.full[stage]);
                 }
             }
@@ -195,13 +203,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     const uint32_t a0 = smem_u32(sA + stage * a_chunk);
                     const uint32_t bh = smem_u32(sB + kc * b_chunk);
                     const uint32_t bl = smem_u32(sB + (kc_n + kc) * b_chunk);
-                    for (int k = 0; k < TC_KCHUNK / 16; k++) {
-                        mma_bf16(d, smem_desc(a0 + 32 * k), smem_desc(bh + 32 * k), idesc, accumulate);
+                    for (int k = 0; k < KW / 16; k++) {
+                        mma_bf16(d, smem_desc_rows<RB>(a0 + 32 * k), smem_desc_rows<RB>(bh + 32 * k), idesc,
+                                 accumulate);
                         accumulate = 1;
                     }
                     if (sp < 2)  // V_hi C_lo, V_mid C_lo (V_lo C_lo dropped)
-                        for (int k = 0; k < TC_KCHUNK / 16; k++)
-                            mma_bf16(d, smem_desc(a0 + 32 * k), smem_desc(bl + 32 * k), idesc, 1);
+                        for (int k = 0; k < KW / 16; k++)
+                            mma_bf16(d, smem_desc_rows<RB>(a0 + 32 * k), smem_desc_rows<RB>(bl + 32 * k),
+                                     idesc, 1);
                     mma_commit(&S.empty[stage]);
                 }
                 if (!ok) break;
@@ -239,17 +249,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     ok = __all_sync(0xffffffffu, !*(volatile int *)S.failed &&
                                                      mbar_wait(&S.full[stage], phase, TC_WAIT_CYCLES));
                 if (ok) {
-                    const unsigned char *rowp = sA + stage * a_chunk + m * 128;
+                    const unsigned char *rowp = sA + stage * a_chunk + m * RB;
                     const int sp = c / kc_n, kc = c % kc_n;
 #pragma unroll
-                    for (int gg = 0; gg < 4 / TC_NSPLIT; gg++) {   // groups 4 kc + split + TC_NSPLIT gg
+                    for (int gg = 0; gg < GPC / TC_NSPLIT; gg++) {   // groups GPC kc + split + TC_NSPLIT gg
 #pragma unroll
                         for (int pc = 0; pc < 2; pc++) {    // 8-colour pieces of the group
                             const int j = 2 * (split + TC_NSPLIT * gg) + pc;
-                            const uint4 q =
-                                *reinterpret_cast<const uint4 *>(rowp + ((j ^ (m & 7)) << 4));
+                            // 16-byte piece j of row m: 128-byte swizzle at j ^ (m % 8),
+                            // 64-byte swizzle at j ^ ((m / 2) % 4)
+                            const int jp = RB == 128 ? (j ^ (m & 7)) : (j ^ ((m >> 1) & 3));
+                            const uint4 q = *reinterpret_cast<const uint4 *>(rowp + (jp << 4));
                             const uint32_t w[4] = {q.x, q.y, q.z, q.w};
-                            float *d = &v[(kc * (4 / TC_NSPLIT) + gg) * 16 + 8 * pc];
+                            float *d = &v[(kc * (GPC / TC_NSPLIT) + gg) * 16 + 8 * pc];
 #pragma unroll
                             for (int i = 0; i < 4; i++) {
                                 const float lo = __uint_as_float(w[i] << 16);
@@ -598,28 +610,34 @@ int mg_tc_parts_per_event(int cpe) {
 }
 
 size_t mg_tc_smem_bytes(int kp, int np) {
-    const int kc_n = kp / TC_KCHUNK;
-    return 1024 + (size_t)2 * kc_n * np * 128 + (size_t)TC_STAGES * TC_M * 128 +
+    const int kw = kp == 32 ? 32 : TC_KCHUNK;   // colours per chunk
+    const int kc_n = kp / kw;
+    return 1024 + (size_t)2 * kc_n * np * 2 * kw + (size_t)TC_STAGES * TC_M * 2 * kw +
            (1 + 2 * TC_STAGES + 4) * 8 + 16;
 }
 
 cudaError_t mg_launch_colorsum_tc(const __nv_bfloat16 *jbuf, long long ncols_alloc, int kp,
                                   const __nv_bfloat16 *cmat, int np, int ncolor, int cpe,
                                   uint32_t extra_tx, double *part, int *err, cudaStream_t stream) {
-    if (ncols_alloc % TC_M || kp % TC_KCHUNK || np % 16 || np > 128 || kp > 2 * TC_KCHUNK ||
-        np > kp || cpe < 8 || (cpe & (cpe - 1)))
+    if (ncols_alloc % TC_M || (kp != 32 && kp != TC_KCHUNK && kp != 2 * TC_KCHUNK) || np % 16 ||
+        np > 128 || np > kp || cpe < 8 || (cpe & (cpe - 1)))
         return cudaErrorInvalidValue;
+    const uint32_t kw = kp == 32 ? 32u : (uint32_t)TC_KCHUNK;   // colours per chunk
     CUtensorMap ma, mb;
-    if (!make_map(&ma, jbuf, (uint64_t)ncols_alloc, (uint64_t)3 * kp, TC_M)) return cudaErrorInvalidValue;
-    if (!make_map(&mb, cmat, (uint64_t)2 * np, (uint64_t)kp, (uint32_t)np)) return cudaErrorInvalidValue;
+    if (!make_map(&ma, jbuf, (uint64_t)ncols_alloc, (uint64_t)3 * kp, TC_M, kw)) return cudaErrorInvalidValue;
+    if (!make_map(&mb, cmat, (uint64_t)2 * np, (uint64_t)kp, (uint32_t)np, kw)) return cudaErrorInvalidValue;
     int np_pad = 32;
     while (np_pad < np) np_pad <<= 1;
     const int tmem_cols = 2 * np_pad;  // two accumulators
     const size_t smem = mg_tc_smem_bytes(kp, np);
-    cudaError_t e = cudaFuncSetAttribute(k_colorsum_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_colorsum_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        kp == 32 ? cudaFuncSetAttribute(k_colorsum_tc<32, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem)
+        : kp == TC_KCHUNK
+            ? cudaFuncSetAttribute(k_colorsum_tc<TC_KCHUNK, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem)
+            : cudaFuncSetAttribute(k_colorsum_tc<TC_KCHUNK, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, nsm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -627,12 +645,15 @@ cudaError_t mg_launch_colorsum_tc(const __nv_bfloat16 *jbuf, long long ncols_all
     const long long ntiles = ncols_alloc / TC_M;
     const long long grid = ntiles < nsm ? ntiles : nsm;   // persistent: one CTA per SM
     mg_note_launch();
-    if (kp == TC_KCHUNK)
-        k_colorsum_tc<1><<<(unsigned)grid, TC_THREADS, smem, stream>>>(ma, mb, np, np_pad, cpe, ntiles,
-                                                                       tmem_cols, extra_tx, part, err);
+    if (kp == 32)
+        k_colorsum_tc<32, 1><<<(unsigned)grid, TC_THREADS, smem, stream>>>(ma, mb, np, np_pad, cpe, ntiles,
+                                                                           tmem_cols, extra_tx, part, err);
+    else if (kp == TC_KCHUNK)
+        k_colorsum_tc<TC_KCHUNK, 1><<<(unsigned)grid, TC_THREADS, smem, stream>>>(
+            ma, mb, np, np_pad, cpe, ntiles, tmem_cols, extra_tx, part, err);
     else
-        k_colorsum_tc<2><<<(unsigned)grid, TC_THREADS, smem, stream>>>(ma, mb, np, np_pad, cpe, ntiles,
-                                                                       tmem_cols, extra_tx, part, err);
+        k_colorsum_tc<TC_KCHUNK, 2><<<(unsigned)grid, TC_THREADS, smem, stream>>>(
+            ma, mb, np, np_pad, cpe, ntiles, tmem_cols, extra_tx, part, err);
     return cudaGetLastError();
 }
 

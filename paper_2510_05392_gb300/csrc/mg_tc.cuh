@@ -71,6 +71,27 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
     return d;
 }
 
+// The same for K-major operands of 32 BF16 per row written by TMA with the
+// 64-byte swizzle (8-row groups 512 bytes apart; layout type 4).
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);      // start address      [0,14)
+    d |= (uint64_t)1 << 16;                         // leading byte offset (unused, swizzled K-major)
+    d |= (uint64_t)(512 >> 4) << 32;                // stride byte offset  [32,46)
+    d |= (uint64_t)1 << 46;                         // descriptor version  [46,48)
+    d |= (uint64_t)4 << 61;                         // 64-byte swizzle     [61,64)
+    return d;
+}
+
+// descriptor of a K-major swizzled operand with `row_bytes` (64 or 128) per row
+template <int ROW_BYTES>
+__device__ __forceinline__ uint64_t smem_desc_rows(uint32_t saddr) {
+    if constexpr (ROW_BYTES == 64)
+        return smem_desc_sw64(saddr);
+    else
+        return smem_desc(saddr);
+}
+
 // Instruction descriptor: kind::f16 with BF16 A/B, FP32 D, both K-major.
 __host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
     return (1u << 4)                 // D format F32
@@ -125,16 +146,19 @@ inline encode_tiled_fn encode_fn() {
     return fn;
 }
 
-// 2-D BF16 tensor map, row-major [rows][cols], box = box_rows x 64, 128B swizzle.
-inline bool make_map(CUtensorMap *m, const void *base, uint64_t rows, uint64_t cols, uint32_t box_rows) {
+// 2-D BF16 tensor map, row-major [rows][cols], box = box_rows x box_cols
+// (64 columns: 128-byte swizzle; 32 columns: 64-byte swizzle).
+inline bool make_map(CUtensorMap *m, const void *base, uint64_t rows, uint64_t cols, uint32_t box_rows,
+                     uint32_t box_cols = TC_KCHUNK) {
     encode_tiled_fn f = encode_fn();
-    if (!f) return false;
+    if (!f || (box_cols != 64 && box_cols != 32)) return false;
     const cuuint64_t dims[2] = {cols, rows};
     const cuuint64_t strides[1] = {cols * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)TC_KCHUNK, box_rows};
+    const cuuint32_t box[2] = {box_cols, box_rows};
     const cuuint32_t estr[2] = {1, 1};
     return f(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box,
-             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             box_cols == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 

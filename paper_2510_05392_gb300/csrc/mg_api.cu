@@ -101,6 +101,7 @@ void free_proc(mg_process *p) {
     cudaFree(p->d_jrow);
     cudaFree(p->d_qpart);
     cudaFree(p->d_sde_item);
+    cudaFree(p->d_kin);
     if (p->own_tab) {
         free((void *)p->own_tab->ops);
         free((void *)p->own_tab->scat);
@@ -270,6 +271,14 @@ int sigmakin_big(mg_process *p, const double *mom, int64_t nevt, double *me, dou
         if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? MG_ERR_NO_MEMORY : cuda_fail(e);
         p->sde_item_cap = nipad_max;
     }
+    if (ev_chunk > p->kin_cap) {
+        cudaFree(p->d_kin);
+        p->d_kin = nullptr;
+        p->kin_cap = 0;
+        cudaError_t e = cudaMalloc(&p->d_kin, mg_big_kin_bytes() * (size_t)ev_chunk);
+        if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? MG_ERR_NO_MEMORY : cuda_fail(e);
+        p->kin_cap = ev_chunk;
+    }
     double *sde_item = want_sde ? p->d_sde_item : nullptr;
     int rc = MG_OK;
     const mg_dev_proc dp = dev_view(p);
@@ -282,7 +291,7 @@ int sigmakin_big(mg_process *p, const double *mom, int64_t nevt, double *me, dou
         int slot = mg_timer_begin(p, s, MG_KT_DIAGRAM);
         if (e == cudaSuccess)
             e = mg_launch_sigmakin_big(dp, mom + e0 * t->npar * 4, nitem, p->d_units, nu, t->nslot,
-                                       t->nslot_top, p->d_scratch, T, p->d_jrow, R, nip, s,
+                                       t->nslot_top, p->d_scratch, T, p->d_jrow, R, nip, p->d_kin, s,
                                        want_sde ? bx->channel : -1,
                                        want_sde && bx->channel_ids ? bx->channel_ids + e0 : nullptr,
                                        sde_item);

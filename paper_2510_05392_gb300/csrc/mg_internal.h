@@ -127,12 +127,13 @@ int mg_big_ngluon();
 int mg_big_block();
 int mg_big_blocks_per_sm(int *out);
 size_t mg_big_state_bytes(int nslot, int nslot_top, int nslot_acc);
+size_t mg_big_kin_bytes();   // kinematic tables of one event
 cudaError_t mg_launch_build_cbig(const long long *row, const signed char *perm, int nc, int np,
                                  double *cbT, cudaStream_t stream);
 cudaError_t mg_launch_sigmakin_big(const mg_dev_proc &dp, const double *mom, long long nitem,
                                    const int *units, int nunits, int nsg, int nsf, double2 *scratch,
                                    long long T, double *jrow, long long R, long long nipad,
-                                   cudaStream_t stream, int channel = -1,
+                                   void *kin, cudaStream_t stream, int channel = -1,
                                    const int *channel_ids = nullptr, double *sde_item = nullptr);
 cudaError_t mg_launch_flow_weights_big(const double *jrow, long long R, long long nipad,
                                        const int *units, int nunits, long long nevt, int ncolor,

@@ -55,6 +55,8 @@ struct mg_process {
     long long qpart_len;
     double *d_sde_item;          // per-item channel sums of one chunk (extras)
     long long sde_item_cap;      // items it holds
+    void *d_kin;                 // kinematic tables of the events of one chunk
+    long long kin_cap;           // events they hold
 };
 
 // kinds of timed launches

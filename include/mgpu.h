@@ -21,13 +21,16 @@
  *                    positive helicity
  *   streams          every compute call is asynchronous and ordered on the
  *                    given cudaStream_t (NULL = legacy default stream).
- *                    mg_sigmakin of an FP64 process compiled into the
- *                    library neither allocates nor synchronises.  The mixed
- *                    precision path, the table-file process and the extras
- *                    keep per-process workspaces grown on demand: the first
- *                    call, and any call with more events than before,
- *                    allocates (cudaFree/cudaMalloc, which can synchronise
- *                    the device); later calls of at most that size do not.
+ *                    Every evaluation path keeps per-process workspaces
+ *                    grown on demand (FP64: the jamp buffer, 64 * ncolor
+ *                    bytes per diagram-kernel thread, used up to 24 GiB and
+ *                    skipped above that or when it cannot be allocated; the
+ *                    mixed precision path, the table-file process and the
+ *                    extras: their own buffers as well): the first call, and
+ *                    any call with more events than before, allocates
+ *                    (cudaFree/cudaMalloc, which can synchronise the
+ *                    device); later calls of at most that size do not.
+ *                    mg_filter_helicities_noalloc never allocates.
  *                    Calls on one process share its workspaces, so they must
  *                    not overlap on the GPU: issue them on one stream (or
  *                    order the streams), or use one process per stream.

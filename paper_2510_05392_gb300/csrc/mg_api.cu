@@ -102,6 +102,7 @@ void free_proc(mg_process *p) {
     cudaFree(p->d_qpart);
     cudaFree(p->d_sde_item);
     cudaFree(p->d_kin);
+    cudaFree(p->d_jg);
     if (p->own_tab) {
         free((void *)p->own_tab->ops);
         free((void *)p->own_tab->scat);
@@ -808,6 +809,31 @@ int mg_filter_helicities(mg_process *p, const double *mom, int64_t n, void *stre
     return MG_OK;
 }
 
+// Jamp buffer of a diagram launch over nevt events (tpe threads each): the
+// jamps of every thread in global memory, updated by reductions at L2
+// (mg_kernels.cu).  Grown on demand and kept; NULL (the jamps then stay in
+// local memory) when it would exceed MG_JAMP_BUFFER_MAX bytes or cannot be
+// allocated.
+static const size_t MG_JAMP_BUFFER_MAX = 24ull << 30;
+
+static double2 *jamp_buffer(mg_process *p, long long nevt, int tpe) {
+    const long long threads = (nevt * tpe + p->block - 1) / p->block * p->block;
+    const size_t bytes = (size_t)threads * 4 * p->tab->ncolor * sizeof(double2);
+    if (bytes > MG_JAMP_BUFFER_MAX) return nullptr;
+    if (bytes > p->jg_bytes) {
+        cudaFree(p->d_jg);
+        p->d_jg = nullptr;
+        p->jg_bytes = 0;
+        if (cudaMalloc(&p->d_jg, bytes) != cudaSuccess) {
+            cudaGetLastError();   // out of memory is not sticky: run without
+            p->d_jg = nullptr;
+            return nullptr;
+        }
+        p->jg_bytes = bytes;
+    }
+    return p->d_jg;
+}
+
 // Mixed precision: per chunk of events, the diagram kernel writes the jamps
 // as BF16 GEMM rows, the tensor-core kernel forms the colour sums, and a small
 // kernel adds each event's partial sums.  The chunk workspace is allocated on
@@ -858,13 +884,14 @@ static int sigmakin_mixed(mg_process *p, const double *mom, int64_t nevt, double
         if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? MG_ERR_NO_MEMORY : cuda_fail(e);
         p->part_len = parts;
     }
+    double2 *jg = jamp_buffer(p, chunk < nevt ? chunk : nevt, tpe);
     const mg_dev_proc dp = dev_view(p);
     for (long long e0 = 0; e0 < nevt; e0 += chunk) {
         const long long n = (nevt - e0 < chunk) ? nevt - e0 : chunk;
         const long long used = (n * cpe + 127) / 128 * 128;
         int slot = mg_timer_begin(p, s, MG_KT_DIAGRAM);
         MG_CUDA(mg_launch_sigmakin(dp, mom + e0 * p->tab->npar * 4, n, p->d_units, p->nunits, tpe,
-                                   p->block, nullptr, nullptr, s, p->d_jbuf, p->kp, nup));
+                                   p->block, nullptr, nullptr, s, p->d_jbuf, p->kp, nup, nullptr, jg));
         mg_timer_end(p, s, slot);
         slot = mg_timer_begin(p, s, MG_KT_COLOUR);
         if (big_tc)
@@ -910,9 +937,10 @@ static int sigmakin_impl(mg_process *p, const double *mom, int64_t nevt, double 
         if (me_hel) return MG_ERR_UNSUPPORTED;
         return sigmakin_mixed(p, mom, nevt, me, tpe, s);
     }
+    double2 *jg = jamp_buffer(p, nevt, tpe);
     const int slot = mg_timer_begin(p, s, MG_KT_DIAGRAM);
     MG_CUDA(mg_launch_sigmakin(dev_view(p), mom, nevt, p->d_units, p->nunits, tpe, p->block, me,
-                               me_hel, s));
+                               me_hel, s, nullptr, 0, 0, nullptr, jg));
     mg_timer_end(p, s, slot);
     return MG_OK;
 }
@@ -1199,7 +1227,7 @@ extern "C" int mg_sigmakin_ex(mg_process *p, const double *mom, int64_t nevt,
     int tpe = p->tpe;
     while (tpe > 1 && tpe > p->nunits) tpe >>= 1;
     MG_CUDA(mg_launch_sigmakin(dev_view(p), mom, nevt, p->d_units, p->nunits, tpe, p->block, me, mh, s,
-                               nullptr, 0, 0, &ex));
+                               nullptr, 0, 0, &ex, jamp_buffer(p, nevt, tpe)));
     if (want_hel || want_col)
         MG_CUDA(mg_launch_select(mh, nhel, jw, nc, nevt, x->rnd_hel_dev, x->rnd_col_dev,
                                  want_hel ? x->hel_out_dev : nullptr, want_col ? x->col_out_dev : nullptr, s));

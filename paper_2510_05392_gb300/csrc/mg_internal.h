@@ -102,10 +102,15 @@ typedef struct {
 // (top, antitop) helicity combinations, bit 2*bt + btb), nunits of them.
 // jout != NULL: write the jamps as tensor-core GEMM rows (no FP64 colour sum,
 // me/me_hel unused); row index ((e * nunits_pad + unit) * 4 + v) * 2 + re/im.
+// jg != NULL: the jamps accumulate there through L2 reductions, jamp (c, v) of
+// thread t at jg[(4 c + v) * T + t] with T = the launch's threads
+// (ceil(nevt * tpe / block) * block), so jg holds 4 * ncolor * T double2;
+// NULL: they stay in local memory.
 cudaError_t mg_launch_sigmakin(const mg_dev_proc &dp, const double *mom, int64_t nevt,
                                const int *units, int nunits, int tpe, int block, double *me,
                                double *me_hel, cudaStream_t stream, __nv_bfloat16 *jout = nullptr,
-                               int kp = 0, int nunits_pad = 0, const mg_extras *extras = nullptr);
+                               int kp = 0, int nunits_pad = 0, const mg_extras *extras = nullptr,
+                               double2 *jg = nullptr);
 cudaError_t mg_launch_select(const double *me_hel, int nhel, const double *jw, int ncolor,
                              long long nevt, const double *rh, const double *rc, int *hel_out,
                              int *col_out, cudaStream_t stream);

@@ -13,7 +13,13 @@
 // GB300 design notes.  The FP64 pipe is the bottleneck of this kernel by a
 // wide margin, so the program is table driven: an op record is a uniform
 // (warp-broadcast) load, the dispatch is warp-uniform, and wavefunctions,
-// jamps and per-event kinematics live in per-thread local memory.  Per-event
+// colour-group sums and per-event kinematics live in per-thread local memory.
+// The jamps accumulate in a per-thread global buffer through FP64 reductions
+// performed at L2 (red.global.add.f64: no wait for the old value, and the
+// additions, about a tenth of the FP64 instructions, leave the FP64 pipe;
+// measured +9% for ggttgg, +12% for ggttggg), then come back into local
+// memory for the colour sum; without a buffer they stay in local memory and
+// are updated in place.  Per-event
 // quantities (momentum sums, 1/P^2, top propagators) are computed once per
 // thread and reused by all of its helicities; gluon wavefunctions are shared
 // by the four top/antitop helicities of a unit (helicity recycling of the
@@ -31,6 +37,20 @@ using namespace mg;
 
 namespace {
 
+__device__ __forceinline__ void red_add(double *p, double v) {
+    asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+
+__device__ __forceinline__ void st_relaxed(double2 *p, double r, double i) {
+    asm volatile("st.relaxed.gpu.global.v2.f64 [%0], {%1, %2};" ::"l"(p), "d"(r), "d"(i) : "memory");
+}
+
+__device__ __forceinline__ cx ld_relaxed(const double2 *p) {
+    double r, i;
+    asm volatile("ld.relaxed.gpu.global.v2.f64 {%0, %1}, [%2];" : "=d"(r), "=d"(i) : "l"(p) : "memory");
+    return mk(r, i);
+}
+
 // One evaluation of the program: gluon-helicity configuration g and all four
 // (top, antitop) helicity combinations v = 2*bt + btb at once.  Gluon
 // wavefunctions (pool WG) are computed once for the four; top-line objects
@@ -40,13 +60,25 @@ namespace {
 // variant v the |D|^2 of the single-diagram-enhancement channel `channel` to
 // sde8[v] and of every channel to sde8[4 + v] (a channel's amplitude is the
 // value of its one diagram term; its colour coefficients have modulus one).
+// With jt (this thread's jamp buffer in global memory, jamp (c, v) at
+// jt[(4 c + v) * js]) the jamp updates are FP64 reductions performed at L2
+// (red.global.add.f64): the thread does not wait for them and the additions
+// leave the FP64 pipe; the finished jamps are then read back into J.  A
+// thread's zeroing stores, reductions and loads of one address are all
+// relaxed (strong) operations, so they take effect in program order and the
+// sums are the ones of the read-modify-write loop.
 template <int NG, int NSG, int NSF, int NSA, int NC>
 __device__ void run_unit(const Kin<NG> &k, int g, const int4 *__restrict__ ops, int nops,
                          const int *__restrict__ scat, const double *__restrict__ cup, double mt,
                          cx (*WG)[4], cx (*WF)[2][4], cx (*G0)[4], cx (*ACC)[4], cx (*J)[4],
-                         double *me4, bool colour_sum, int channel = -1, double *sde8 = nullptr) {
-    for (int c = 0; c < NC; c++)
-        for (int v = 0; v < 4; v++) J[c][v] = mk(0.0, 0.0);
+                         double *me4, bool colour_sum, int channel = -1, double *sde8 = nullptr,
+                         double2 *jt = nullptr, long long js = 0) {
+    if (jt) {
+        for (int i = 0; i < 4 * NC; i++) st_relaxed(jt + i * js, 0.0, 0.0);
+    } else {
+        for (int c = 0; c < NC; c++)
+            for (int v = 0; v < 4; v++) J[c][v] = mk(0.0, 0.0);
+    }
     for (int i = 0; i < nops; i++) {
         const int4 a = __ldg(ops + 2 * i);
         const int4 b = __ldg(ops + 2 * i + 1);
@@ -133,10 +165,23 @@ __device__ void run_unit(const Kin<NG> &k, int g, const int4 *__restrict__ ops, 
                     if (!(mode & 8)) break;
                     for (int v = 0; v < 4; v++) amp[v] = ACC[b.z][v];
                 }
+                const int end = b.x + b.y;
+                if (jt) {
+                    for (int s = b.x; s < end; s++) {
+                        const int e = __ldg(scat + s);
+                        double2 *jc = jt + (long long)(4 * (e >> 2)) * js;
+#pragma unroll
+                        for (int v = 0; v < 4; v++) {
+                            const cx t = unit_times(e, amp[v]);
+                            red_add(&jc[v * js].x, t.r);
+                            red_add(&jc[v * js].y, t.i);
+                        }
+                    }
+                    break;
+                }
                 // jamp updates in pairs: the flows of one scatter list are
                 // distinct, so both old values are loaded before either store
                 // and the two loads wait for memory together
-                const int end = b.x + b.y;
                 int s = b.x;
                 for (; s + 1 < end; s += 2) {
                     const int e0 = __ldg(scat + s), e1 = __ldg(scat + s + 1);
@@ -163,6 +208,9 @@ __device__ void run_unit(const Kin<NG> &k, int g, const int4 *__restrict__ ops, 
                 break;
         }
     }
+    if (jt)
+        for (int c = 0; c < NC; c++)
+            for (int v = 0; v < 4; v++) J[c][v] = ld_relaxed(jt + (4LL * c + v) * js);
     if (!colour_sum) return;
     // colour sum over the packed upper triangle (diagonal D*C_ii, off-diagonal
     // 2*D*C_ij), the four helicity combinations sharing each matrix entry
@@ -234,9 +282,11 @@ __global__ void __launch_bounds__(EX ? 256 : 128, EX ? 1 : 3)
                int nops, const int *__restrict__ scat, const double *__restrict__ cup,
                const int *__restrict__ units, int nunits, int tpe, double mt, double wt,
                double factor, double *__restrict__ me, double *__restrict__ me_hel,
-               __nv_bfloat16 *__restrict__ jout, int kp, int nunits_pad, mg_extras ex) {
+               __nv_bfloat16 *__restrict__ jout, int kp, int nunits_pad, mg_extras ex,
+               double2 *__restrict__ jg) {
     constexpr int NPAR = NG + 2;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long js = (long long)gridDim.x * blockDim.x;   // jamp buffer stride
     const long long e = t / tpe;
     const int s = (int)(t - e * tpe);
     double sum = 0.0;
@@ -268,7 +318,8 @@ __global__ void __launch_bounds__(EX ? 256 : 128, EX ? 1 : 3)
             if (EX)
                 for (int q = 0; q < 8; q++) sde8[q] = 0.0;
             run_unit<NG, NSG, NSF, NSA, NC>(k, g, ops, nops, scat, cup, mt, WG, WF, G0, ACC, J, me4,
-                                            !jout, channel, (EX && ex.sde) ? sde8 : nullptr);
+                                            !jout, channel, (EX && ex.sde) ? sde8 : nullptr,
+                                            jg ? jg + t : nullptr, js);
             if (jout) {
                 write_jamp_rows<NC>(J, mask, jout, (e * nunits_pad + iu) * 8, kp);
                 continue;
@@ -433,7 +484,7 @@ __global__ void k_helmask(const double *__restrict__ mh, long long n, int nhel, 
 cudaError_t mg_launch_sigmakin(const mg_dev_proc &dp, const double *mom, int64_t nevt,
                                const int *units, int nunits, int tpe, int block, double *me,
                                double *me_hel, cudaStream_t stream, __nv_bfloat16 *jout, int kp,
-                               int nunits_pad, const mg_extras *extras) {
+                               int nunits_pad, const mg_extras *extras, double2 *jg) {
     mg_extras ex;
     if (extras) {
         ex = *extras;
@@ -456,11 +507,11 @@ cudaError_t mg_launch_sigmakin(const mg_dev_proc &dp, const double *mom, int64_t
         if (extras)                                                                              \
             k_sigmakin<NG, NSG, NSF, NSA, NC, true><<<(unsigned)grid, block, 0, stream>>>(       \
                 mom, nevt, reinterpret_cast<const int4 *>(dp.ops), dp.nops, dp.scat, dp.cup,      \
-                units, nunits, tpe, dp.mt, dp.wt, dp.factor, me, me_hel, jout, kp, nunits_pad, ex); \
+                units, nunits, tpe, dp.mt, dp.wt, dp.factor, me, me_hel, jout, kp, nunits_pad, ex, jg); \
         else                                                                                     \
             k_sigmakin<NG, NSG, NSF, NSA, NC, false><<<(unsigned)grid, block, 0, stream>>>(      \
                 mom, nevt, reinterpret_cast<const int4 *>(dp.ops), dp.nops, dp.scat, dp.cup,      \
-                units, nunits, tpe, dp.mt, dp.wt, dp.factor, me, me_hel, jout, kp, nunits_pad, ex); \
+                units, nunits, tpe, dp.mt, dp.wt, dp.factor, me, me_hel, jout, kp, nunits_pad, ex, jg); \
         break;
         MG_PROC_LIST(MG_LAUNCH)
 #undef MG_LAUNCH

@@ -28,6 +28,8 @@ struct mg_process {
     int jbuf_nunits;             // unit count the buffer's padding was zeroed for
     double *d_part;              // partial colour sums of one chunk
     long long part_len;
+    double2 *d_jg;               // jamps of every thread of a diagram launch
+    size_t jg_bytes;
     int *d_err;                  // device error word of the bounded waits
     uint32_t debug_extra_tx;     // test hook: extra bytes the TMA barrier expects
     // per-event extras (mg_sigmakin_ex): cached workspaces

@@ -184,7 +184,7 @@ def _measured_peak(key):
 
 _KERNEL_SOURCES = {
     "k_sigmakin": ["mg_kernels.cu", "mg_kin.cuh", "mg_dirac.cuh", "mg_internal.h"],
-    "k_colorsum_tc": ["mg_colorsum_tc.cu", "mg_internal.h"],
+    "k_colorsum_tc": ["mg_colorsum_tc.cu", "mg_tc.cuh", "mg_internal.h"],
 }
 
 

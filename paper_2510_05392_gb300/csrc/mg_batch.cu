@@ -28,6 +28,8 @@ struct mg_batch {
     mg_batch_item *d_items;
     int *d_units;                       // the blocks' work-unit lists, copied at creation
     unsigned long long *d_counter;
+    double2 *d_jg;                      // jamp buffers of the persistent kernel's threads
+    int max_ncolor;                     // largest colour-flow count of the items
     long long total_slots;
     int nsm, ctas_per_sm, max_ctas_per_sm;
     int device;
@@ -66,7 +68,7 @@ int upload(mg_batch *b) {
 
 int launch(mg_batch *b, cudaStream_t s) {
     cudaError_t e = mg_launch_batch(b->d_items, b->n, b->d_counter, b->total_slots,
-                                    b->nsm * b->ctas_per_sm, s);
+                                    b->nsm * b->ctas_per_sm, s, b->d_jg);
     return e == cudaSuccess ? MG_OK : mg_cuda_fail(e);
 }
 
@@ -77,6 +79,7 @@ void free_batch(mg_batch *b) {
     cudaFree(b->d_items);
     cudaFree(b->d_units);
     cudaFree(b->d_counter);
+    cudaFree(b->d_jg);
     delete b;
 }
 
@@ -134,6 +137,7 @@ int mg_batch_create(int nproc, mg_process *const *procs, const double *const *mo
         while (tpe > 1 && tpe > p->nunits) tpe >>= 1;
         it.tpe = tpe;
         it.table_index = dp.table_index;
+        if (p->tab->ncolor > b->max_ncolor) b->max_ncolor = p->tab->ncolor;
         b->items.push_back(it);
         b->order.push_back(i);
     }
@@ -160,6 +164,11 @@ int mg_batch_create(int nproc, mg_process *const *procs, const double *const *mo
     b->ctas_per_sm = b->max_ctas_per_sm;
     cudaError_t e = cudaMalloc(&b->d_items, sizeof(mg_batch_item) * nproc);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(unsigned long long));
+    // jamp buffers for the largest grid the autotuner may launch (jamp
+    // updates as L2 reductions, as in mg_sigmakin)
+    if (e == cudaSuccess && b->max_ncolor > 0)
+        e = cudaMalloc(&b->d_jg, sizeof(double2) * 4 * (size_t)b->max_ncolor *
+                                     (size_t)b->nsm * b->max_ctas_per_sm * 128);
     // the batch's own copy of every block's work-unit list (at most 128 units
     // each), so that a later helicity filter of a process does not change the
     // captured launch under it

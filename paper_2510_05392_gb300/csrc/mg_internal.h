@@ -169,9 +169,12 @@ cudaError_t mg_launch_colorsum_tc_big(const __nv_bfloat16 *jb, long long R, int 
                                       const __nv_bfloat16 *cmat, int np, uint32_t extra_tx,
                                       double *part, int *err, cudaStream_t stream);
 int mg_tc_parts_per_event(int cpe);
-// persistent multi-process kernel: counter reset + one launch of grid CTAs
+// persistent multi-process kernel: counter reset + one launch of grid CTAs of
+// 128 threads; jg (may be NULL): the threads' jamp buffers, 4 * (largest
+// ncolor) * grid * 128 double2
 cudaError_t mg_launch_batch(const mg_batch_item *d_items, int nitems, unsigned long long *d_counter,
-                            long long total_slots, int grid, cudaStream_t stream);
+                            long long total_slots, int grid, cudaStream_t stream,
+                            double2 *jg = nullptr);
 int mg_batch_ctas_per_sm(int *out);
 int mg_sigmakin_occupancy(int table_index, int block, int *ctas_per_sm);
 #define MG_BATCH_MAX_NGLUON 5   // processes the persistent kernel carries

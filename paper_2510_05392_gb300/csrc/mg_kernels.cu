@@ -402,8 +402,10 @@ __global__ void k_select(const double *__restrict__ me_hel, int nhel, const doub
 // event.  All 32 lanes of a warp call this for the same item (the shuffles
 // below span the warp).  Kept out of line so that the persistent kernel's
 // stack frame is the largest of the carried processes, not their sum.
+// jt: this thread's jamp buffer (stride js), or NULL.
 template <int NG, int NSG, int NSF, int NSA, int NC>
-__device__ __noinline__ void batch_slot(const mg_batch_item &it, long long slot) {
+__device__ __noinline__ void batch_slot(const mg_batch_item &it, long long slot, double2 *jt,
+                                        long long js) {
     constexpr int NPAR = NG + 2;
     const int tpe = it.tpe;
     const long long e = slot / tpe;
@@ -422,7 +424,7 @@ __device__ __noinline__ void batch_slot(const mg_batch_item &it, long long slot)
             const int u = __ldg(it.units + iu);
             double me4[4];
             run_unit<NG, NSG, NSF, NSA, NC>(k, u >> 4, ops, it.nops, it.scat, it.cup, it.mt, WG, WF,
-                                            G0, ACC, J, me4, true);
+                                            G0, ACC, J, me4, true, -1, nullptr, jt, js);
             for (int v = 0; v < 4; v++)
                 if ((u >> v) & 1) sum += me4[v];
         }
@@ -432,16 +434,21 @@ __device__ __noinline__ void batch_slot(const mg_batch_item &it, long long slot)
 }
 
 template <int NG, int NSG, int NSF, int NSA, int NC>
-__device__ __forceinline__ void batch_dispatch(const mg_batch_item &it, long long slot) {
-    if constexpr (NG <= MG_BATCH_MAX_NGLUON) batch_slot<NG, NSG, NSF, NSA, NC>(it, slot);
+__device__ __forceinline__ void batch_dispatch(const mg_batch_item &it, long long slot, double2 *jt,
+                                               long long js) {
+    if constexpr (NG <= MG_BATCH_MAX_NGLUON) batch_slot<NG, NSG, NSF, NSA, NC>(it, slot, jt, js);
 }
 
 // Persistent kernel: every warp repeatedly takes the next 32 slots from the
 // global counter until all items are done (no waits on other threads).
+// jg (may be NULL): jamp buffers, thread t's jamp (c, v) at
+// jg[(4 c + v) * T + t], T = the launch's threads.
 __global__ void __launch_bounds__(128, 3)
     k_batch(const mg_batch_item *__restrict__ items, int nitems,
-            unsigned long long *__restrict__ counter, long long total_slots) {
+            unsigned long long *__restrict__ counter, long long total_slots, double2 *__restrict__ jg) {
     const int lane = threadIdx.x & 31;
+    const long long js = (long long)gridDim.x * blockDim.x;
+    double2 *jt = jg ? jg + (long long)blockIdx.x * blockDim.x + threadIdx.x : nullptr;
     for (;;) {
         unsigned long long base = 0;
         if (lane == 0) base = atomicAdd(counter, 32ULL);
@@ -454,7 +461,7 @@ __global__ void __launch_bounds__(128, 3)
         switch (it.table_index) {
 #define MG_BATCH_CASE(IDX, NG, NSG, NSF, NSA, NC) \
     case IDX:                                     \
-        batch_dispatch<NG, NSG, NSF, NSA, NC>(it, slot); \
+        batch_dispatch<NG, NSG, NSF, NSA, NC>(it, slot, jt, js); \
         break;
             MG_PROC_LIST(MG_BATCH_CASE)
 #undef MG_BATCH_CASE
@@ -529,12 +536,12 @@ cudaError_t mg_launch_helmask(const double *me_hel, int64_t n, int nhel, double 
 }
 
 cudaError_t mg_launch_batch(const mg_batch_item *d_items, int nitems, unsigned long long *d_counter,
-                            long long total_slots, int grid, cudaStream_t stream) {
+                            long long total_slots, int grid, cudaStream_t stream, double2 *jg) {
     cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), stream);
     if (e != cudaSuccess) return e;
     if (total_slots <= 0) return cudaSuccess;
     mg_note_launch();
-    k_batch<<<grid, 128, 0, stream>>>(d_items, nitems, d_counter, total_slots);
+    k_batch<<<grid, 128, 0, stream>>>(d_items, nitems, d_counter, total_slots, jg);
     return cudaGetLastError();
 }
 

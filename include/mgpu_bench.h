@@ -26,6 +26,14 @@ int mg_probe_fp64_peak(int blocks, int iters, int reps, double *flops_out);
 struct mg_process;
 int mg_debug_inject_stall(struct mg_process *p, unsigned int extra_bytes);
 
+/* Test hook for the jamp buffer of the diagram kernel (processes compiled
+ * into the library): enable = 0 makes later calls on p update the jamps in
+ * place in local memory instead of through FP64 reductions at L2 into the
+ * per-process jamp buffer; 1 (the default) restores the buffer.  Both paths
+ * form every jamp as the same sum in the same order, so their results are
+ * bit-identical.  Returns MG_OK or MG_ERR_BAD_ARG (p NULL). */
+int mg_debug_jamp_buffer(struct mg_process *p, int enable);
+
 /* The same test hook for the surrogate's tensor-core GEMMs: every later GEMM
  * launch of s makes its operand barrier expect extra_bytes more than its TMA
  * copies deliver, so the MMA thread's bounded wait runs out (about a second

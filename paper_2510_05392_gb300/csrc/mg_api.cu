@@ -819,7 +819,7 @@ static const size_t MG_JAMP_BUFFER_MAX = 24ull << 30;
 static double2 *jamp_buffer(mg_process *p, long long nevt, int tpe) {
     const long long threads = (nevt * tpe + p->block - 1) / p->block * p->block;
     const size_t bytes = (size_t)threads * 4 * p->tab->ncolor * sizeof(double2);
-    if (bytes > MG_JAMP_BUFFER_MAX) return nullptr;
+    if (p->jg_off || bytes > MG_JAMP_BUFFER_MAX) return nullptr;
     if (bytes > p->jg_bytes) {
         cudaFree(p->d_jg);
         p->d_jg = nullptr;
@@ -1164,6 +1164,12 @@ extern "C" int mg_device_status(mg_process *p, void *stream) {
 extern "C" int mg_debug_inject_stall(mg_process *p, unsigned int extra_bytes) {
     if (!p) return MG_ERR_BAD_ARG;
     p->debug_extra_tx = extra_bytes;
+    return MG_OK;
+}
+
+extern "C" int mg_debug_jamp_buffer(mg_process *p, int enable) {
+    if (!p) return MG_ERR_BAD_ARG;
+    p->jg_off = enable ? 0 : 1;
     return MG_OK;
 }
 

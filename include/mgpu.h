@@ -257,7 +257,10 @@ void mg_process_destroy(mg_process *p);
  *
  * mg_batch_create records the blocks (device pointers momenta[i]
  * [nevt[i]][npar_i][4] and me_out[i] [nevt[i]], owned by the caller and read
- * on every run) and copies each process's current helicity list (a later
+ * on every run), allocates the jamp buffers of the persistent kernel's
+ * threads (64 x the largest colour-flow count bytes per thread, about 0.45
+ * GB on a GB300 when a 5-gluon process is in the batch) and copies each
+ * process's current helicity list (a later
  * mg_filter_helicities of a process does not change the batch); the batch
  * reads its processes' device tables on every run, so it must be destroyed
  * before any of them; mg_batch_run replays the launch as a CUDA graph (captured on

@@ -31,8 +31,11 @@ int mg_debug_inject_stall(struct mg_process *p, unsigned int extra_bytes);
  * place in local memory instead of through FP64 reductions at L2 into the
  * per-process jamp buffer; 1 (the default) restores the buffer.  Both paths
  * form every jamp as the same sum in the same order, so their results are
- * bit-identical.  Returns MG_OK or MG_ERR_BAD_ARG (p NULL). */
-int mg_debug_jamp_buffer(struct mg_process *p, int enable);
+ * bit-identical.  max_bytes > 0 replaces the buffer limit (24 GiB; an FP64
+ * call whose buffer would exceed it runs as several launches of whole waves
+ * of events, or of as many events as fit), 0 restores it.  Returns MG_OK or
+ * MG_ERR_BAD_ARG (p NULL, max_bytes < 0). */
+int mg_debug_jamp_buffer(struct mg_process *p, int enable, int64_t max_bytes);
 
 /* The same test hook for the surrogate's tensor-core GEMMs: every later GEMM
  * launch of s makes its operand barrier expect extra_bytes more than its TMA

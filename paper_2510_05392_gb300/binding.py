@@ -77,7 +77,7 @@ _SIGS = {
     "mg_device_status": ([_VP, _VP], ctypes.c_int),
     "mg_sigmakin_ex": ([_VP, _VP, ctypes.c_int64, ctypes.POINTER(mg_sigmakin_extras), _VP, _VP], ctypes.c_int),
     "mg_debug_inject_stall": ([_VP, ctypes.c_uint], ctypes.c_int),
-    "mg_debug_jamp_buffer": ([_VP, ctypes.c_int], ctypes.c_int),
+    "mg_debug_jamp_buffer": ([_VP, ctypes.c_int, ctypes.c_int64], ctypes.c_int),
     "mg_filter_helicities_noalloc": ([_VP, _VP, ctypes.c_int64, _VP, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "mg_batch_create": ([ctypes.c_int, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_VP), ctypes.POINTER(_VP)], ctypes.c_int),
     "mg_batch_run": ([_VP, _VP], ctypes.c_int),

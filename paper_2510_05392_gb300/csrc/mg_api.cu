@@ -816,10 +816,14 @@ int mg_filter_helicities(mg_process *p, const double *mom, int64_t n, void *stre
 // allocated.
 static const size_t MG_JAMP_BUFFER_MAX = 24ull << 30;
 
+static size_t jamp_buffer_max(const mg_process *p) {
+    return p->jg_max ? p->jg_max : MG_JAMP_BUFFER_MAX;
+}
+
 static double2 *jamp_buffer(mg_process *p, long long nevt, int tpe) {
     const long long threads = (nevt * tpe + p->block - 1) / p->block * p->block;
     const size_t bytes = (size_t)threads * 4 * p->tab->ncolor * sizeof(double2);
-    if (p->jg_off || bytes > MG_JAMP_BUFFER_MAX) return nullptr;
+    if (p->jg_off || bytes > jamp_buffer_max(p)) return nullptr;
     if (bytes > p->jg_bytes) {
         cudaFree(p->d_jg);
         p->d_jg = nullptr;
@@ -832,6 +836,23 @@ static double2 *jamp_buffer(mg_process *p, long long nevt, int tpe) {
         p->jg_bytes = bytes;
     }
     return p->d_jg;
+}
+
+// Events per FP64 diagram launch: all of them when their jamp buffer fits
+// the buffer limit, else whole waves of the kernel's resident threads whose
+// buffer does (the call then runs as several launches).
+static long long fp64_chunk(mg_process *p, long long nevt, int tpe) {
+    const long long per_event = (long long)tpe * 4 * p->tab->ncolor * (long long)sizeof(double2);
+    const long long cap = (long long)jamp_buffer_max(p) / per_event - p->block;   // block rounding
+    if (nevt <= cap || cap <= 0) return nevt;
+    int nsm = 0, occ = 1;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess ||
+        mg_sigmakin_occupancy(p->table_index, p->block, &occ) != MG_OK) {
+        cudaGetLastError();
+        return cap;
+    }
+    const long long wave = (long long)nsm * occ * p->block / tpe;   // events per wave
+    return (wave > 0 && cap >= wave) ? cap / wave * wave : cap;
 }
 
 // Mixed precision: per chunk of events, the diagram kernel writes the jamps
@@ -937,11 +958,17 @@ static int sigmakin_impl(mg_process *p, const double *mom, int64_t nevt, double 
         if (me_hel) return MG_ERR_UNSUPPORTED;
         return sigmakin_mixed(p, mom, nevt, me, tpe, s);
     }
-    double2 *jg = jamp_buffer(p, nevt, tpe);
-    const int slot = mg_timer_begin(p, s, MG_KT_DIAGRAM);
-    MG_CUDA(mg_launch_sigmakin(dev_view(p), mom, nevt, p->d_units, p->nunits, tpe, p->block, me,
-                               me_hel, s, nullptr, 0, 0, nullptr, jg));
-    mg_timer_end(p, s, slot);
+    const long long chunk = fp64_chunk(p, nevt, tpe);
+    double2 *jg = jamp_buffer(p, chunk, tpe);
+    const int npar = p->tab->npar;
+    for (long long e0 = 0; e0 < nevt; e0 += chunk) {
+        const long long n = nevt - e0 < chunk ? nevt - e0 : chunk;
+        const int slot = mg_timer_begin(p, s, MG_KT_DIAGRAM);
+        MG_CUDA(mg_launch_sigmakin(dev_view(p), mom + e0 * npar * 4, n, p->d_units, p->nunits, tpe,
+                                   p->block, me ? me + e0 : nullptr, me_hel ? me_hel + e0 * nhel : nullptr,
+                                   s, nullptr, 0, 0, nullptr, jg));
+        mg_timer_end(p, s, slot);
+    }
     return MG_OK;
 }
 
@@ -1167,9 +1194,10 @@ extern "C" int mg_debug_inject_stall(mg_process *p, unsigned int extra_bytes) {
     return MG_OK;
 }
 
-extern "C" int mg_debug_jamp_buffer(mg_process *p, int enable) {
-    if (!p) return MG_ERR_BAD_ARG;
+extern "C" int mg_debug_jamp_buffer(mg_process *p, int enable, int64_t max_bytes) {
+    if (!p || max_bytes < 0) return MG_ERR_BAD_ARG;
     p->jg_off = enable ? 0 : 1;
+    p->jg_max = (size_t)max_bytes;
     return MG_OK;
 }
 
@@ -1232,8 +1260,19 @@ extern "C" int mg_sigmakin_ex(mg_process *p, const double *mom, int64_t nevt,
     ex.jw = jw;
     int tpe = p->tpe;
     while (tpe > 1 && tpe > p->nunits) tpe >>= 1;
-    MG_CUDA(mg_launch_sigmakin(dev_view(p), mom, nevt, p->d_units, p->nunits, tpe, p->block, me, mh, s,
-                               nullptr, 0, 0, &ex, jamp_buffer(p, nevt, tpe)));
+    const long long chunk = fp64_chunk(p, nevt, tpe);
+    double2 *jg = jamp_buffer(p, chunk, tpe);
+    for (long long e0 = 0; e0 < nevt; e0 += chunk) {
+        const long long n = nevt - e0 < chunk ? nevt - e0 : chunk;
+        mg_extras exc = ex;   // the chunk's slice of every per-event array
+        if (exc.alphas) exc.alphas += e0;
+        if (exc.channel_ids) exc.channel_ids += e0;
+        if (exc.sde) exc.sde += e0;
+        if (exc.jw) exc.jw += e0 * nc;
+        MG_CUDA(mg_launch_sigmakin(dev_view(p), mom + e0 * p->tab->npar * 4, n, p->d_units, p->nunits,
+                                   tpe, p->block, me ? me + e0 : nullptr, mh ? mh + e0 * nhel : nullptr, s,
+                                   nullptr, 0, 0, &exc, jg));
+    }
     if (want_hel || want_col)
         MG_CUDA(mg_launch_select(mh, nhel, jw, nc, nevt, x->rnd_hel_dev, x->rnd_col_dev,
                                  want_hel ? x->hel_out_dev : nullptr, want_col ? x->col_out_dev : nullptr, s));

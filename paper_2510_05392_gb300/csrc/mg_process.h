@@ -31,6 +31,7 @@ struct mg_process {
     double2 *d_jg;               // jamps of every thread of a diagram launch
     size_t jg_bytes;
     int jg_off;                  // test hook: 1 = jamps updated in local memory
+    size_t jg_max;               // test hook: buffer limit in bytes (0: the default)
     int *d_err;                  // device error word of the bounded waits
     uint32_t debug_extra_tx;     // test hook: extra bytes the TMA barrier expects
     // per-event extras (mg_sigmakin_ex): cached workspaces

@@ -39,14 +39,15 @@ def _process(ng, sqrts, **kw):
     return p
 
 
-def _both(p, run):
-    """run() with the jamp buffer, then with in-place updates (numpy copies)."""
+def _both(p, run, first=(1, 0), second=(0, 0)):
+    """run() under two settings (enable, max_bytes) of the jamp-buffer hook
+    (default: buffer, then in-place updates); numpy copies of the outputs."""
     L = binding.lib()
-    assert L.mg_debug_jamp_buffer(p.handle, 1) == binding.MG_OK
+    assert L.mg_debug_jamp_buffer(p.handle, *first) == binding.MG_OK
     a = [x.cpu().numpy().copy() for x in run()]
-    assert L.mg_debug_jamp_buffer(p.handle, 0) == binding.MG_OK
+    assert L.mg_debug_jamp_buffer(p.handle, *second) == binding.MG_OK
     b = [x.cpu().numpy().copy() for x in run()]
-    assert L.mg_debug_jamp_buffer(p.handle, 1) == binding.MG_OK
+    assert L.mg_debug_jamp_buffer(p.handle, 1, 0) == binding.MG_OK
     return a, b
 
 
@@ -110,5 +111,50 @@ def test_extras_bit_identical():
         assert np.array_equal(x, y), np.abs(x - y).max()
 
 
-def test_hook_rejects_null_process():
-    assert binding.lib().mg_debug_jamp_buffer(None, 0) == binding.MG_ERR_BAD_ARG
+def test_large_calls_split_into_launches_bit_identical():
+    """An FP64 call whose jamp buffer exceeds the limit runs as several
+    launches over consecutive event ranges (here a 1 MB limit: 42 events of
+    g g > t t~ g g per launch, 25 launches); |M|^2, the per-helicity values and the extras
+    (alpha_s, channel weights, flow weights) of every event equal those of
+    one launch over all events."""
+    ng = 2
+    sqrts, n = CASES[ng]
+    p = _process(ng, sqrts)
+    nc = p.info().ncolor
+    nhel = 1 << (ng + 4)
+    mom = _gpu(_events(ng, n, 730, sqrts))
+    chan = torch.from_numpy(np.arange(n, dtype=np.int32) % 15).cuda()
+    alphas = torch.from_numpy(0.118 * (1.0 + 0.1 * np.sin(np.arange(n)))).cuda()
+
+    def run():
+        me = torch.empty(n, dtype=torch.float64, device="cuda")
+        me2 = torch.empty(n, dtype=torch.float64, device="cuda")
+        mh = torch.empty(n * nhel, dtype=torch.float64, device="cuda")
+        me3 = torch.empty(n, dtype=torch.float64, device="cuda")
+        sde = torch.empty(n, dtype=torch.float64, device="cuda")
+        flow = torch.empty(n * nc, dtype=torch.float64, device="cuda")
+        p.sigmakin(mom, me)
+        p.sigmakin_hel(mom, me2, mh)
+        p.sigmakin_ex(mom, out=me3, alphas=alphas, sde=sde, flow=flow, channel_ids=chan)
+        torch.cuda.synchronize()
+        return me, me2, mh, me3, sde, flow
+
+    a, b = _both(p, run, first=(1, 0), second=(1, 1 << 20))
+    L = binding.lib()
+    assert L.mg_debug_jamp_buffer(p.handle, 1, 1 << 20) == binding.MG_OK
+    p.set_kernel_timing(64)
+    p.sigmakin(mom, torch.empty(n, dtype=torch.float64, device="cuda"))
+    launches = p.kernel_times(reset=True)["diagram"][1]
+    p.set_kernel_timing(0)
+    assert L.mg_debug_jamp_buffer(p.handle, 1, 0) == binding.MG_OK
+    assert launches == 25, launches
+    assert np.all(a[0] > 0)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y), np.abs(x - y).max()
+
+
+def test_hook_rejects_bad_arguments():
+    L = binding.lib()
+    assert L.mg_debug_jamp_buffer(None, 0, 0) == binding.MG_ERR_BAD_ARG
+    p = binding.Process("g g > t t~")
+    assert L.mg_debug_jamp_buffer(p.handle, 1, -1) == binding.MG_ERR_BAD_ARG

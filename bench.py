@@ -293,13 +293,16 @@ def run_batch(args):
     for _ in range(args.warmup):
         b.run(stream)
     torch.cuda.synchronize(dev)
+    clocks = Clocks(dev.index) if not args.no_clocks else None
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):
         b.run(stream)
     ev1.record(stream)
     torch.cuda.synchronize(dev)
+    clk = clocks.stop() if clocks else None
     t_batch = ev0.elapsed_time(ev1) / 1e3
+    in_bytes = sum(m.numel() * m.element_size() for _, m, _ in blocks)
     # the same blocks, one launch per process
     ev0.record(stream)
     for _ in range(args.steps):
@@ -316,10 +319,12 @@ def run_batch(args):
         "config": {"workload": "uneven_batch_4proc", "blocks": [[pr, n] for pr, _, n in BATCH_BLOCKS],
                    "launch": "one persistent kernel per step, CUDA-graph replay",
                    "autotuned": {"threads_per_event": tpe, "ctas_per_sm": ctas,
-                                 "tuning_ms_per_step": tuned_ms}},
+                                 "tuning_ms_per_step": tuned_ms},
+                   "l2": f"not flushed: the steps' inputs ({in_bytes / 1e6:.0f} MB of momenta) exceed L2"},
         "per_process_launches_events_per_s": total * args.steps / t_seq,
         "roofline": _fp64_roofline(flops_step, t_batch / args.steps, "k_batch (whole step)", peak),
         "gpu_launches": args.steps,
+        "clocks": clk,
     }
     print(json.dumps(line), flush=True)
 
@@ -456,6 +461,7 @@ def run_surrogate(args):
     nex = ctypes.c_int64()
     two_runs = []
     launches_two = 0
+    clocks = Clocks(dev.index) if not args.no_clocks else None   # over the two-stage runs
     for k in range(args.seeds):
         rng = np.random.default_rng(seed + 200 + k)
         u1d, u2d = (torch.from_numpy(rng.uniform(size=ncand)).to(dev) for _ in range(2))
@@ -474,6 +480,8 @@ def run_surrogate(args):
         a_ = acc.cpu().numpy() != 0
         two_runs.append({"seconds": t_two, "exact_evaluations": int(nex.value), "accepted": int(a_.sum()),
                          "ess": ess(wts[a_]), "ess_per_s": ess(wts[a_]) / t_two})
+
+    clk = clocks.stop() if clocks else None
 
     def mean_err(xs):
         m = float(np.mean(xs))
@@ -506,6 +514,7 @@ def run_surrogate(args):
                               "ess_per_s": pl_m, "ess_per_s_err": pl_e},
         "surrogate_gain_ess_per_s": gain, "surrogate_gain_err": gain_err,
         "gpu_launches": launches_two,
+        "clocks": clk,
     }
     print(json.dumps(line), flush=True)
     L.mg_sur_destroy(h)

@@ -23,8 +23,9 @@
  *                    given cudaStream_t (NULL = legacy default stream).
  *                    Every evaluation path keeps per-process workspaces
  *                    grown on demand (FP64: the jamp buffer, 64 * ncolor
- *                    bytes per diagram-kernel thread, used up to 24 GiB and
- *                    skipped above that or when it cannot be allocated; the
+ *                    bytes per diagram-kernel thread, at most 24 GiB: a
+ *                    larger call runs as several launches, and the jamps stay
+ *                    in local memory when it cannot be allocated; the
  *                    mixed precision path, the table-file process and the
  *                    extras: their own buffers as well): the first call, and
  *                    any call with more events than before, allocates

@@ -814,8 +814,8 @@ int mg_filter_helicities(mg_process *p, const double *mom, int64_t n, void *stre
 // Jamp buffer of a diagram launch over nevt events (tpe threads each): the
 // jamps of every thread in global memory, updated by reductions at L2
 // (mg_kernels.cu).  Grown on demand and kept; NULL (the jamps then stay in
-// local memory) when it would exceed MG_JAMP_BUFFER_MAX bytes or cannot be
-// allocated.
+// local memory) when it would exceed the limit (MG_JAMP_BUFFER_MAX, or the
+// test hook's) or cannot be allocated; fp64_chunk keeps FP64 calls within it.
 static const size_t MG_JAMP_BUFFER_MAX = 24ull << 30;
 
 static size_t jamp_buffer_max(const mg_process *p) {

@@ -712,9 +712,13 @@ def _cpu_info():
             break
         except (KeyError, ValueError):
             pass
-    if mhz is None:
+    for path in ("/sys/devices/system/cpu/cpu0/cpufreq/cpuinfo_max_freq",
+                 "/sys/devices/system/cpu/cpufreq/policy0/cpuinfo_max_freq",
+                 "/sys/devices/system/cpu/cpu0/cpufreq/scaling_max_freq"):
+        if mhz is not None:
+            break
         try:
-            with open("/sys/devices/system/cpu/cpu0/cpufreq/cpuinfo_max_freq") as fh:
+            with open(path) as fh:
                 mhz = int(fh.read().strip()) / 1000.0
         except (OSError, ValueError):
             pass
@@ -810,6 +814,8 @@ def run_ours(args):
                "sample": f"first {ns} events of {name}, {dt:.1f} s",
                "value_1core": v1, "sample_1core": f"first {n1} events of {name}, {dt1:.1f} s",
                "cpu_model": model, "cpu_max_mhz": mhz, "nproc": os.cpu_count()}
+        if mhz is None:
+            cpu["cpu_clock_note"] = "not exposed on this host (lscpu lists no MHz, no cpufreq files)"
 
     if rank == 0:
         line = {

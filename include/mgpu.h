@@ -30,7 +30,9 @@
  *                    extras: their own buffers as well): the first call, and
  *                    any call with more events than before, allocates
  *                    (cudaFree/cudaMalloc, which can synchronise the
- *                    device); later calls of at most that size do not.
+ *                    device); later calls of at most that size do not (so
+ *                    before capturing calls in a CUDA graph, make one call
+ *                    of at least the captured size outside the capture).
  *                    mg_filter_helicities_noalloc never allocates.
  *                    Calls on one process share its workspaces, so they must
  *                    not overlap on the GPU: issue them on one stream (or
